@@ -1,0 +1,344 @@
+"""Benchmark: checkerboard Cabibbo-Marinari SU(3) heatbath sweeps on GB300.
+
+Workload (one GPU): a 32^4 periodic lattice, beta = 6.0, Haar-random (hot)
+start from the seed, FP32 12-real link storage with FP64 re-unitarisation
+and FP64 measurement reductions, FHKP with 2 hits.  One step = 10 sweeps,
+then a re-unitarisation and a plaquette + Polyakov-loop measurement (the
+re-unitarise-every-10 cadence of the workload), all inside the library's
+stage machine; 100 steps = the 1000-sweep run.  The links (201 MB) are
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Metric: SU(3) link updates per second (whole job over all ranks).
+With --gpus N > 1 every rank runs its own chain (replicas: the method needs
+no exchange between independent chains), weak scaling.
+
+--impl reference times the plain double-precision CPU oracle on this
+workload (a bounded slice of it per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = [32, 32, 32, 32]
+BETA = 6.0
+HITS = 2
+SWEEPS_PER_STEP = 10
+SEED = 20090406
+METRIC = "SU(3) link updates/s"
+UNIT = "link updates/s"
+WORKLOAD = "32^4 PBC SU(3) Wilson, beta=6.0, hot start, CM heatbath with FHKP 2 hits, FP32 12-real links, " \
+           "FP64 reunitarize + plaquette/Polyakov every 10 sweeps; step = 10 sweeps"
+
+
+def nlinks():
+    n = 1
+    for d in DIMS:
+        n *= d
+    return n * len(DIMS)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("su3_device.cuh", "su3_kernels.cu", "su3_engine.h"):
+        with open(os.path.join(ROOT, "paper_0904_0642_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    h = kernel_hash()
+    for ln in lines:
+        t = ln.split()
+        if len(t) >= 3 and not ln.startswith("#") and t[0] == kernel and t[1] == h:
+            return float(t[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return None
+        rows = []
+        for ln in open(self.path):
+            t = [x.strip() for x in ln.split(",")]
+            if len(t) < 9:
+                continue
+            try:
+                rows.append((float(t[1]), float(t[2]), float(t[3]), t[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step updates one bounded slice
+    (2^17 sites of one checkerboard colour, i.e. 65536 links) of the 32^4
+    hot-start lattice in double precision on one host core."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    lat = oracle.Lattice(DIMS).hot_start(SEED)
+    slice_sites = 1 << 17
+    V = lat.V
+    ups = []
+    t_total = 0.0
+    for step in range(args.warmup + args.steps):
+        colour = step % 2
+        mu = (step // 2) % 4
+        s0 = (step * slice_sites) % V
+        t0 = time.perf_counter()
+        prop, acc = lat.phase(BETA, HITS, SEED, sweep=0, colour=colour, mu=mu, s_begin=s0, s_end=s0 + slice_sites)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            t_total += dt
+            ups.append(slice_sites // 2)
+    value = sum(ups) / t_total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_step": "one FP64 oracle update of 65536 links "
+                                                               "(one colour, one direction, 2^17 sites)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} slices of 65536 link updates of the 32^4 hot-start lattice"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline():
+    """One full oracle sweep of the 32^4 hot-start lattice on one core."""
+    import oracle
+    lat = oracle.Lattice(DIMS).hot_start(SEED)
+    t0 = time.perf_counter()
+    lat.sweep(BETA, HITS, SEED, n=1)
+    dt = time.perf_counter() - t0
+    return {"value": lat.nlinks / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one full sweep (4194304 link updates) of the 32^4 hot-start lattice, single thread, FP64",
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e / FP64 / roofline passes")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shape (for profiler runs)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_0904_0642_gb300 as su3
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.Stream()
+    lat = su3.Lattice(DIMS, beta=BETA, seed=SEED + rank, hits=HITS, storage=su3.SU3_FP32_12,
+                      start=su3.SU3_START_HOT, reunit_every=SWEEPS_PER_STEP, measure_every=SWEEPS_PER_STEP,
+                      measure_capacity=4096, stream=stream)
+    if args.no_autotune:
+        threads, ctas, us = 128, 0, None
+    else:
+        threads, ctas, us = lat.autotune()
+    links = lat.nlinks
+    for _ in range(args.warmup):
+        lat.sweep(SWEEPS_PER_STEP)
+    torch.cuda.synchronize()
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            lat.sweep(SWEEPS_PER_STEP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms)
+    value = world * args.steps * SWEEPS_PER_STEP * links / (ms_max * 1e-3)
+    meas = lat.measurements()
+    plaq_last = float(meas[-1, 1, 0]) if len(meas) else float("nan")
+    launches = args.steps * (2 * len(DIMS) * SWEEPS_PER_STEP + 2)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "links": links,
+                       "sweeps_per_step": SWEEPS_PER_STEP, "storage": "FP32 12-real", "hits": HITS, "beta": BETA,
+                       "l2": "inputs larger than L2 (201 MB of links vs 129 MB L2); no flush",
+                       "launch": {"threads": threads, "ctas_per_sm": ctas, "autotune_us_per_sweep": us},
+                       "graph": True, "parallelism": f"replicas x{world}"},
+            "gpu_launches": launches, "plaquette_last": plaq_last}
+    clocks = clk.summary()
+    line["clocks"] = clocks
+
+    if not args.no_extras:
+        # Roofline: live per-kernel CUDA-event timing of the update-phase launches.
+        peaks, peak_src = measured_peaks()
+        lat.set_profiling(True)
+        lat.profile(reset=True)
+        lat.sweep(SWEEPS_PER_STEP)
+        prof = lat.profile(reset=True)
+        lat.set_profiling(False)
+        upd_ms = prof["update_ms"] / max(1, prof["update_launches"])
+        V = links // len(DIMS)
+        alg_bytes = (V // 2) * (2 * len(DIMS) + 1) * 48
+        achieved = alg_bytes / (upd_ms * 1e-3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": achieved / peaks["hbm_gbs"], "traffic": recorded_traffic("k_tick_fp32_update"),
+                            "peak_source": f"hbm_gbs of {peak_src}", "kernel": "k_tick<StoreF32x12> update phase",
+                            "alg_bytes_per_launch": alg_bytes, "avg_launch_us": upd_ms * 1e3,
+                            "reunit_us": 1e3 * prof["reunit_ms"] / max(1, prof["reunit_launches"]),
+                            "measure_us": 1e3 * prof["measure_ms"] / max(1, prof["measure_launches"])}
+
+        # End to end through the C ABI: each step uploads the step's input
+        # configuration from pinned host memory (canonical FP64 layout),
+        # runs the 10 sweeps + re-unitarisation, and reads the plaquette and
+        # Polyakov loop back to the host.
+        host_in = torch.empty((links * 18,), dtype=torch.float64, pin_memory=True).numpy()
+        host_in[:] = lat.get_links().reshape(-1)
+        k_e2e = max(3, args.steps // 10)
+        lat.sweep(SWEEPS_PER_STEP)  # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            lat.set_links(host_in)
+            lat.sweep(SWEEPS_PER_STEP)
+            lat.plaquette()
+            lat.polyakov()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        line["e2e"] = {"value": world * k_e2e * SWEEPS_PER_STEP * links / t_e2e, "unit": UNIT,
+                       "h2d_bytes_per_step": links * 18 * 8, "d2h_bytes_per_step": 2 * 3 * 5 * 8,
+                       "steps": k_e2e}
+
+        # Plain FP64 single chain, 18-real storage, same workload and seed.
+        lat64 = su3.Lattice(DIMS, beta=BETA, seed=SEED + rank, hits=HITS, storage=su3.SU3_FP64_18,
+                            start=su3.SU3_START_HOT, reunit_every=SWEEPS_PER_STEP, stream=stream)
+        ref32 = su3.Lattice(DIMS, beta=BETA, seed=SEED + rank, hits=HITS, storage=su3.SU3_FP32_12,
+                            start=su3.SU3_START_HOT, reunit_every=SWEEPS_PER_STEP, stream=stream)
+        lat64.sweep(SWEEPS_PER_STEP)
+        ref32.sweep(SWEEPS_PER_STEP)
+        p64 = lat64.plaquette()[0]
+        p32 = ref32.plaquette()[0]
+        torch.cuda.synchronize()
+        k64 = 3
+        e0.record(stream)
+        for _ in range(k64):
+            lat64.sweep(SWEEPS_PER_STEP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(e0.elapsed_time(e1))
+        line["fp64_single_chain"] = {"value": world * k64 * SWEEPS_PER_STEP * links / (ms64 * 1e-3), "unit": UNIT,
+                                     "steps": k64, "storage": "FP64 18-real"}
+        line["plaquette_fp32_vs_fp64_after_10_sweeps"] = {"fp32": p32, "fp64": p64, "abs_diff": abs(p32 - p64)}
+        ref32.close()
+        lat64.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

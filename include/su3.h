@@ -1,0 +1,258 @@
+/*
+ * su3.h -- C ABI of libsu3gb300: the checkerboard Cabibbo-Marinari heatbath
+ * of pure SU(3) Wilson-action lattice gauge theory on one GB300 GPU
+ * (sm_103a), after B. A. Berg, "Fortran MPI Checkerboard Code for SU(3)
+ * Lattice Gauge Theory I" (arXiv:0904.0642).
+ *
+ * Conventions shared by every call
+ * ---------------------------------
+ * - Geometry (Sec. 2, eqs. i_s, xD, x^i, i_c): D directions, extents
+ *   n^1..n^D (all even: the checkerboard needs it), site number
+ *   i_s - 1 = sum_i x^i n_a^i with x^1 running fastest, colour
+ *   mod(sum_i x^i, 2).  Direction D is time.
+ * - Boundary (Sec. 2.2): SU3_PBC is the torus.  SU3_DLT is the
+ *   double-layered torus: two identical lattices (layers 0 and 1); a step
+ *   across the boundary of a glued direction lands on the other layer.
+ * - Action (Sec. 2.1, Table 2): weight exp((beta/3) sum_p Re Tr U_p),
+ *   beta = 6/g^2.
+ * - Canonical host layout of links: double U[layer][site][mu][row][col][re,im]
+ *   (18 doubles per link; D*V*layers links).  Device storage is internal.
+ * - Random numbers: Philox4x32-10 with key = seed and counter
+ *   (site key, sweep, tag(colour, mu, subgroup, hit), purpose), so every
+ *   result is a deterministic function of (configuration, seed, sweep
+ *   counter) and does not depend on launch shape, batching or graph use.
+ * - Errors: every call returns an su3_status; nothing throws across the
+ *   ABI.  On error, su3_last_error() returns a message (thread-local).
+ * - Streams: a handle runs all its work on the cudaStream_t given at
+ *   creation (NULL: a stream the library creates and owns; graphs
+ *   cannot capture the legacy default stream).  Calls that return host
+ *   values synchronise that stream; the others are asynchronous.
+ * - Ownership: handles are owned by the caller and freed with the matching
+ *   destroy call.  A caller-owned link buffer must outlive its handle.
+ */
+#ifndef SU3_GB300_H
+#define SU3_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SU3_OK = 0,
+  SU3_EINVAL = -1,    /* invalid argument (odd extent, D out of range, beta < 0, hits < 1, ...) */
+  SU3_ENOMEM = -2,    /* device allocation failed or HBM budget exceeded */
+  SU3_ECUDA = -3,     /* a CUDA runtime call failed */
+  SU3_ETIMEOUT = -4,  /* a bounded wait ran out */
+  SU3_EBUSY = -5,     /* result not ready yet */
+  SU3_ENOTFOUND = -6  /* unknown job id */
+} su3_status;
+
+typedef enum { SU3_PBC = 0, SU3_DLT = 1 } su3_boundary;
+
+/* Device link storage.  FP64_18: all 18 reals in double.  FP32_12: the first
+ * two rows in float, the third rebuilt as conj(row1 x row2) on load. */
+typedef enum { SU3_FP64_18 = 0, SU3_FP32_12 = 1 } su3_storage;
+
+typedef enum { SU3_START_COLD = 0, SU3_START_HOT = 1 } su3_start;
+
+#define SU3_MAX_D 4 /* GPU kernels are compiled for D = 2, 3, 4 */
+
+typedef struct su3_config {
+  int32_t D;                    /* 2..SU3_MAX_D */
+  int32_t dims[SU3_MAX_D];      /* n^1..n^D, even, >= 2 */
+  int32_t boundary;             /* su3_boundary */
+  int32_t glue_mask;            /* DLT: bit mu glues direction mu; 0 means all directions */
+  double beta;                  /* >= 0 */
+  uint64_t seed;                /* Philox key */
+  int32_t storage;              /* su3_storage */
+  int32_t start;                /* su3_start: ordered (all links 1) or Haar-random (Sec. 2.4, istart) */
+  int32_t hits;                 /* FHKP proposals per SU(2) subgroup (Sec. 2.1, nhit), >= 1 */
+  int32_t reunit_every;         /* re-unitarise every k sweeps inside su3_sweep (0: never) */
+  int32_t measure_every;        /* record plaquette + Polyakov loop every k sweeps (0: never) */
+  int32_t measure_capacity;     /* ring size of recorded measurements (0: 1024) */
+  int32_t layer_blind;          /* DLT: identical random numbers on both layers (Sec. 3.2, lat2test) */
+  int32_t rng_period[SU3_MAX_D];/* random-number site key uses x^i mod period (0: n^i); Sec. 3.1.1 test */
+  void *stream;                 /* cudaStream_t, or NULL */
+  void *link_buffer;            /* optional caller-owned device buffer for the links, or NULL */
+  size_t link_buffer_bytes;     /* its size; must be >= su3_link_bytes() */
+} su3_config;
+
+typedef struct su3_lattice su3_lattice;
+
+/* Fill *cfg with defaults: D=4, 4^4, PBC, beta=6, seed=1, FP64_18, cold,
+ * hits=2, no automatic re-unitarisation or measurement. */
+void su3_config_init(su3_config *cfg);
+
+/* Device bytes the links of cfg need (0 if cfg is invalid). */
+size_t su3_link_bytes(const su3_config *cfg);
+
+/* Create a lattice: torus or DLT of the given extents, cold start, FP64_18
+ * storage, beta, seed.  Validation as for su3_lattice_create_ex.  *out is
+ * NULL on error. */
+su3_status su3_lattice_create(int D, const int *dims, su3_boundary boundary, double beta, uint64_t seed,
+                              su3_lattice **out);
+
+/* Create a lattice from a full configuration.  EINVAL when D is outside
+ * 2..SU3_MAX_D, an extent is odd or < 2, beta < 0, hits < 1, a period does
+ * not divide its extent (or is odd), or the caller buffer is too small;
+ * ENOMEM when the device allocation fails.  The start configuration is
+ * written before return (asynchronously on the stream). */
+su3_status su3_lattice_create_ex(const su3_config *cfg, su3_lattice **out);
+
+/* Release the handle and its device memory (not a caller-owned buffer). */
+void su3_lattice_destroy(su3_lattice *lat);
+
+/* n checkerboard sweeps (Sec. 2.1: every link updated once, colour by
+ * colour, direction by direction), each link by Cabibbo-Marinari over the
+ * SU(2) subgroups (1,2), (1,3), (2,3) with the multi-hit FHKP heatbath
+ * (`hits` proposals, the subgroup kept when none is accepted).  Honours
+ * reunit_every and measure_every.  Asynchronous.  EINVAL for n < 0 or
+ * hits < 1. */
+su3_status su3_sweep(su3_lattice *lat, int n, int hits);
+
+/* Re-unitarise every link (Sec. 2.4, su3reunit): Gram-Schmidt of rows 1, 2
+ * in double precision, row 3 = conj(row1 x row2).  Asynchronous. */
+su3_status su3_reunitarize(su3_lattice *lat);
+
+/* Plaquette averages (Sec. 2.4 wloops, Table 2): (1/3) Re Tr U_p over the
+ * plaquettes whose base site is in `layer` (layer = -1: the whole lattice),
+ * total, space-like and time-like (time-like planes contain direction D;
+ * *space is 0 when D = 2).  Double-precision accumulation with a fixed
+ * reduction order.  Synchronises the stream.  Output pointers are host
+ * pointers and may be NULL. */
+su3_status su3_plaquette(su3_lattice *lat, int layer, double *total, double *space, double *time);
+
+/* Polyakov loop: (1/3) Tr of the ordered product of U_D along the closed
+ * line through (layer, x, x^D = 0) (length n^D, or 2 n^D on a DLT glued in
+ * time), averaged over the spatial sites of the layer (-1: all layers).
+ * Synchronises the stream.  Not in the paper. */
+su3_status su3_polyakov(su3_lattice *lat, int layer, double *re, double *im);
+
+/* Asynchronous measurement into device memory: writes 5 doubles per layer
+ * slot, slots 0..layers-1 then the whole lattice, as
+ * [total, space, time, poly_re, poly_im], to the device pointer out. */
+su3_status su3_measure_async(su3_lattice *lat, double *device_out);
+
+/* Measurements recorded by measure_every, oldest first: up to max entries
+ * of 5*(layers+1) doubles each (layout as su3_measure_async) copied to the
+ * host buffer; *count receives the number copied.  Synchronises. */
+su3_status su3_measurements(su3_lattice *lat, double *host_out, size_t max, size_t *count);
+
+/* Copy all links to / from the host in the canonical layout; n is the
+ * number of doubles in the host buffer (>= 18 * links).  set_links rounds
+ * to the storage precision (FP32_12 keeps rows 1 and 2).  Synchronous. */
+su3_status su3_get_links(su3_lattice *lat, double *host, size_t n);
+su3_status su3_set_links(su3_lattice *lat, const double *host, size_t n);
+
+/* Counters: FHKP proposals and accepted proposals since creation, and the
+ * number of completed sweeps (the sweep counter of the random numbers). */
+su3_status su3_stats(su3_lattice *lat, uint64_t *proposals, uint64_t *accepts, uint64_t *sweeps);
+
+/* Set the sweep counter (resume from a checkpoint taken with su3_get_links
+ * and su3_stats: the counter-based random numbers make the continuation
+ * bitwise identical). */
+su3_status su3_set_sweep_counter(su3_lattice *lat, uint64_t sweeps);
+
+/* Number of links (D*V*layers) and device bytes of the link storage. */
+su3_status su3_lattice_info(su3_lattice *lat, size_t *links, size_t *bytes);
+
+/* Launch shape: threads per block (multiple of 32, 32..1024) and CTAs per SM
+ * of the persistent update grid (0: from the occupancy calculator).  The
+ * random numbers do not depend on it, so results are identical for every
+ * shape.  su3_autotune times the candidates on this lattice (it advances
+ * a scratch copy, not the lattice) and keeps the fastest. */
+su3_status su3_set_launch(su3_lattice *lat, int threads, int ctas_per_sm);
+su3_status su3_autotune(su3_lattice *lat, int *threads, int *ctas_per_sm, double *us_per_sweep);
+
+/* Capture the sweep in a CUDA graph (on = 1) or launch kernel by kernel
+ * (on = 0).  Results are identical either way. */
+su3_status su3_use_graph(su3_lattice *lat, int on);
+
+/* Kernel timing.  With profiling on, su3_sweep launches its ticks one by
+ * one (no graph) with a CUDA event pair around each on the handle's stream,
+ * and su3_get_profile sums the device time per stage kind: update phases,
+ * re-unitarisations, measurements (synchronises; reset = 1 clears).  The
+ * results do not change. */
+typedef struct su3_profile {
+  double update_ms;
+  int64_t update_launches;
+  double reunit_ms;
+  int64_t reunit_launches;
+  double measure_ms;
+  int64_t measure_launches;
+} su3_profile;
+
+su3_status su3_set_profiling(su3_lattice *lat, int on);
+su3_status su3_get_profile(su3_lattice *lat, su3_profile *out, int reset);
+
+/* ---------------------------------------------------------------- ensembles
+ * Many independent chains (each with its own extents, boundary, beta, seed
+ * and hits; one storage for all) advanced together: one fused persistent
+ * launch per checkerboard phase covers every chain.  A chain gives the same
+ * links in an ensemble as alone, bit for bit. */
+typedef struct su3_ensemble su3_ensemble;
+
+su3_status su3_ensemble_create(const su3_config *cfgs, int nchains, void *stream, su3_ensemble **out);
+void su3_ensemble_destroy(su3_ensemble *ens);
+/* n sweeps of every chain (hits from each config). */
+su3_status su3_ensemble_sweep(su3_ensemble *ens, int n);
+/* Plaquette and Polyakov loop of every chain, whole lattice: out[5*c + k],
+ * k = total, space, time, poly_re, poly_im.  Synchronises. */
+su3_status su3_ensemble_measure(su3_ensemble *ens, double *host_out);
+su3_status su3_ensemble_get_links(su3_ensemble *ens, int chain, double *host, size_t n);
+su3_status su3_ensemble_set_launch(su3_ensemble *ens, int threads, int ctas_per_sm);
+su3_status su3_ensemble_use_graph(su3_ensemble *ens, int on);
+/* As su3_set_profiling / su3_get_profile; stages are classified by chain 0. */
+su3_status su3_ensemble_set_profiling(su3_ensemble *ens, int on);
+su3_status su3_ensemble_get_profile(su3_ensemble *ens, su3_profile *out, int reset);
+
+/* ---------------------------------------------------------------- serving
+ * A job server with continuous batching: submitted jobs wait in a queue,
+ * are admitted when a slot and enough of the HBM budget are free, run
+ * together in the fused launch (each chain at its own phase), and retire
+ * when their sweeps are done, which frees memory for the queue. */
+typedef struct su3_server su3_server;
+
+typedef struct su3_job {
+  su3_config cfg;          /* lattice of the job (stream and link_buffer ignored) */
+  int32_t sweeps;          /* sweeps to run, >= 1 */
+} su3_job;
+
+typedef struct su3_result {
+  uint64_t job_id;
+  int32_t status;          /* su3_status of the job */
+  int32_t nlayers;
+  double plaquette[3];     /* whole lattice after the last sweep: total, space, time */
+  double polyakov[2];
+  double layer_plaquette[2];  /* per layer, total */
+  uint64_t proposals, accepts;
+  double submit_s, start_s, finish_s;  /* host clock (seconds since server creation) */
+} su3_result;
+
+/* hbm_budget_bytes: device bytes the resident chains may hold (0: 80 % of
+ * free memory); max_slots: resident chains at most. */
+su3_status su3_server_create(size_t hbm_budget_bytes, int max_slots, su3_server **out);
+/* Queue a job; never blocks.  EINVAL for a bad job, ENOMEM when the job
+ * alone exceeds the budget. */
+su3_status su3_server_submit(su3_server *srv, const su3_job *job, uint64_t *job_id);
+/* EBUSY while queued or running, OK with *out filled once done, ENOTFOUND
+ * for an unknown (or already collected) id. */
+su3_status su3_server_poll(su3_server *srv, uint64_t job_id, su3_result *out);
+su3_status su3_server_wait(su3_server *srv, uint64_t job_id, double timeout_s, su3_result *out);
+/* Jobs queued, resident, and finished-but-uncollected. */
+su3_status su3_server_load(su3_server *srv, int *queued, int *resident, int *finished);
+/* Stops the scheduler; jobs still queued or running end with SU3_EBUSY. */
+void su3_server_destroy(su3_server *srv);
+
+/* Thread-local message of the last error (empty string if none). */
+const char *su3_last_error(void);
+/* Library version string. */
+const char *su3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SU3_GB300_H */

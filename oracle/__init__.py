@@ -65,7 +65,9 @@ def _configure(L):
     L.orc_link_heatbath.argtypes = [dp, dp, c_double, c_int, c_uint64, c_uint32, c_uint32, c_int, c_int,
                                     POINTER(c_uint64)]
     L.orc_link_chain.argtypes = [dp, dp, c_double, c_int, c_uint64, c_int64, dp]
-    L.orc_sweep.argtypes = [gp, dp, c_double, c_int, c_uint64, c_int64, c_int, POINTER(c_uint64), dp]
+    L.orc_sweep.argtypes = [gp, dp, c_double, c_int, c_uint64, c_int64, c_int, POINTER(c_uint64), dp, dp]
+    L.orc_phase.argtypes = [gp, dp, c_double, c_int, c_uint64, c_int64, c_int, c_int, c_int64, c_int64,
+                            POINTER(c_uint64), dp, dp]
     L.orc_reunitarize.argtypes = [gp, dp]
     L.orc_reunitarize_matrix.argtypes = [dp]
     L.orc_plaquette.argtypes = [gp, dp, c_int, dp]
@@ -206,16 +208,28 @@ class Lattice:
         self.sweeps_done = 0
         return self
 
-    def sweep(self, beta: float, hits: int, seed: int, n: int = 1, sweep0: int | None = None, margins=None):
-        """n checkerboard sweeps; returns [proposals, accepts].  margins, if given,
-        is a float64 array of nlinks entries that receives per-link minimum
-        accept-test margins."""
+    def sweep(self, beta: float, hits: int, seed: int, n: int = 1, sweep0: int | None = None, margins=None,
+              kmins=None):
+        """n checkerboard sweeps; returns [proposals, accepts].  margins and
+        kmins, if given, are float64 arrays of nlinks entries (initialised to
+        +inf) that receive per link the smallest accept-test margin and the
+        smallest SU(2) subgroup norm k seen."""
         if sweep0 is None:
             sweep0 = self.sweeps_done
         st = (c_uint64 * 2)()
         mp = _dp(margins) if margins is not None else None
-        lib().orc_sweep(self._g(), _dp(self.U), beta, hits, seed, sweep0, n, st, mp)
+        kp = _dp(kmins) if kmins is not None else None
+        lib().orc_sweep(self._g(), _dp(self.U), beta, hits, seed, sweep0, n, st, mp, kp)
         self.sweeps_done = sweep0 + n
+        return int(st[0]), int(st[1])
+
+    def phase(self, beta: float, hits: int, seed: int, sweep: int, colour: int, mu: int, s_begin: int = 0,
+              s_end: int | None = None):
+        """One (colour, direction) phase over sites [s_begin, s_end) of each
+        layer; returns [proposals, accepts]."""
+        st = (c_uint64 * 2)()
+        lib().orc_phase(self._g(), _dp(self.U), beta, hits, seed, sweep, colour, mu, s_begin,
+                        self.V if s_end is None else s_end, st, None, None)
         return int(st[0]), int(st[1])
 
     def reunitarize(self):

@@ -468,6 +468,7 @@ static const int orc_pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
 typedef struct {
   uint64_t proposals, accepts;
   double margin;
+  double kmin; /* smallest subgroup norm k seen (how well v = a/k is determined) */
 } orc_link_stats;
 
 static void orc_cm_update(mat3 *U, const mat3 *A, double beta, int hits, uint64_t seed, uint32_t site_key,
@@ -481,6 +482,7 @@ static void orc_cm_update(mat3 *U, const mat3 *A, double beta, int hits, uint64_
     a[2] = 0.5 * (creal(W.m[i][j]) - creal(W.m[j][i]));
     a[3] = 0.5 * (cimag(W.m[i][i]) - cimag(W.m[j][j]));
     double k = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+    if (k < st->kmin) st->kmin = k;
     if (k < 1e-300) continue;
     double v[4] = {a[0] / k, a[1] / k, a[2] / k, a[3] / k};
     double alpha = 2.0 * beta * k / 3.0;
@@ -510,7 +512,7 @@ static void orc_cm_update(mat3 *U, const mat3 *A, double beta, int hits, uint64_
 void orc_link_heatbath(double *u18, const double *A18, double beta, int hits, uint64_t seed, uint32_t site_key,
                        uint32_t sweep, int colour, int mu, uint64_t stats[2]) {
   mat3 U = m_load(u18), A = m_load(A18);
-  orc_link_stats st = {0, 0, INFINITY};
+  orc_link_stats st = {0, 0, INFINITY, INFINITY};
   orc_cm_update(&U, &A, beta, hits, seed, site_key, sweep, colour, mu, &st);
   m_store(u18, &U);
   if (stats) { stats[0] += st.proposals; stats[1] += st.accepts; }
@@ -521,7 +523,7 @@ void orc_link_heatbath(double *u18, const double *A18, double beta, int hits, ui
 void orc_link_chain(double *u18, const double *A18, double beta, int hits, uint64_t seed, int64_t n,
                     double *retr_ua) {
   mat3 U = m_load(u18), A = m_load(A18);
-  orc_link_stats st = {0, 0, INFINITY};
+  orc_link_stats st = {0, 0, INFINITY, INFINITY};
   for (int64_t t = 0; t < n; ++t) {
     orc_cm_update(&U, &A, beta, hits, seed, 0u, (uint32_t)t, 0, 0, &st);
     mat3 UA = m_mul(&U, &A);
@@ -538,33 +540,41 @@ void orc_link_chain(double *u18, const double *A18, double beta, int hits, uint6
 /* order of sites inside one (colour, direction) phase does not matter;   */
 /* here it is increasing i_s, layer by layer.                             */
 /* stats (may be NULL): [proposals, accepts] accumulated.                 */
-/* margins (may be NULL): per link, the smallest accept-test margin seen  */
-/* in these sweeps (canonical link order, initialised by the caller).     */
+/* margins, kmins (may be NULL): per link, the smallest accept-test margin */
+/* and the smallest subgroup norm k seen in these sweeps (canonical link  */
+/* order, initialised by the caller).                                     */
 /* ------------------------------------------------------------------ */
 
+/* One (colour, direction) phase over the sites s_begin <= i_s - 1 < s_end
+ * of every layer (the whole phase for [0, V)). */
+void orc_phase(const orc_geom *g, double *U, double beta, int hits, uint64_t seed, int64_t sweep, int colour, int mu,
+               int64_t s_begin, int64_t s_end, uint64_t *stats, double *margins, double *kmins) {
+  int64_t V = orc_nsites(g);
+  if (s_end > V) s_end = V;
+  for (int l = 0; l < g->nlayers; ++l)
+    for (int64_t s = s_begin; s < s_end; ++s) {
+      int32_t x[ORC_MAXD];
+      orc_site_coords(g, s, x);
+      if (orc_colour(g, x) != colour) continue;
+      mat3 A = orc_staple_m(g, U, l, s, mu);
+      double *p = (double *)link_ptr(g, U, l, s, mu);
+      mat3 Ul = m_load(p);
+      orc_link_stats st = {0, 0, INFINITY, INFINITY};
+      orc_cm_update(&Ul, &A, beta, hits, seed, orc_site_key(g, l, s), (uint32_t)sweep, colour, mu, &st);
+      m_store(p, &Ul);
+      if (stats) { stats[0] += st.proposals; stats[1] += st.accepts; }
+      int64_t idx = ((int64_t)l * V + s) * g->D + mu;
+      if (margins && st.margin < margins[idx]) margins[idx] = st.margin;
+      if (kmins && st.kmin < kmins[idx]) kmins[idx] = st.kmin;
+    }
+}
+
 void orc_sweep(const orc_geom *g, double *U, double beta, int hits, uint64_t seed, int64_t sweep0, int nsweeps,
-               uint64_t *stats, double *margins) {
+               uint64_t *stats, double *margins, double *kmins) {
   int64_t V = orc_nsites(g);
   for (int64_t sw = sweep0; sw < sweep0 + nsweeps; ++sw)
     for (int colour = 0; colour < 2; ++colour)
-      for (int mu = 0; mu < g->D; ++mu)
-        for (int l = 0; l < g->nlayers; ++l)
-          for (int64_t s = 0; s < V; ++s) {
-            int32_t x[ORC_MAXD];
-            orc_site_coords(g, s, x);
-            if (orc_colour(g, x) != colour) continue;
-            mat3 A = orc_staple_m(g, U, l, s, mu);
-            double *p = (double *)link_ptr(g, U, l, s, mu);
-            mat3 Ul = m_load(p);
-            orc_link_stats st = {0, 0, INFINITY};
-            orc_cm_update(&Ul, &A, beta, hits, seed, orc_site_key(g, l, s), (uint32_t)sw, colour, mu, &st);
-            m_store(p, &Ul);
-            if (stats) { stats[0] += st.proposals; stats[1] += st.accepts; }
-            if (margins) {
-              int64_t idx = ((int64_t)l * V + s) * g->D + mu;
-              if (st.margin < margins[idx]) margins[idx] = st.margin;
-            }
-          }
+      for (int mu = 0; mu < g->D; ++mu) orc_phase(g, U, beta, hits, seed, sw, colour, mu, 0, V, stats, margins, kmins);
 }
 
 /* ------------------------------------------------------------------ */

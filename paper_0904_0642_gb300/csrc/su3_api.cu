@@ -1,0 +1,1254 @@
+// su3_api.cu -- host runtime and C ABI of libsu3gb300 (see include/su3.h).
+//
+// An Engine owns a set of resident chains (lattices), their device
+// descriptors and stage machines, the tile map of the fused launch, and an
+// optional CUDA graph of ticks.  su3_lattice is an Engine with one chain,
+// su3_ensemble one with many, su3_server one whose chain set changes as
+// jobs are admitted and retired.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/su3.h"
+#include "su3_engine.h"
+#include "su3_launch.h"
+
+using namespace su3g;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+
+static su3_status fail(su3_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CU(expr)                                                                                \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(e_ == cudaErrorMemoryAllocation ? SU3_ENOMEM : SU3_ECUDA, "%s: %s (%s:%d)", #expr, \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                                  \
+  } while (0)
+
+#define TRY(expr)                      \
+  do {                                 \
+    su3_status s_ = (expr);            \
+    if (s_ != SU3_OK) return s_;       \
+  } while (0)
+
+extern "C" const char *su3_last_error(void) { return g_err.c_str(); }
+extern "C" const char *su3_version(void) { return "su3gb300 1.0 (sm_103a)"; }
+
+// ------------------------------------------------------------------ configuration
+
+extern "C" void su3_config_init(su3_config *c) {
+  std::memset(c, 0, sizeof *c);
+  c->D = 4;
+  for (int i = 0; i < SU3_MAX_D; ++i) c->dims[i] = 4;
+  c->boundary = SU3_PBC;
+  c->beta = 6.0;
+  c->seed = 1;
+  c->storage = SU3_FP64_18;
+  c->start = SU3_START_COLD;
+  c->hits = 2;
+}
+
+static su3_status validate(const su3_config *c) {
+  if (!c) return fail(SU3_EINVAL, "config is NULL");
+  if (c->D < 2 || c->D > SU3_MAX_D) return fail(SU3_EINVAL, "D=%d outside 2..%d", c->D, SU3_MAX_D);
+  long long V = 1;
+  for (int i = 0; i < c->D; ++i) {
+    if (c->dims[i] < 2 || (c->dims[i] & 1))
+      return fail(SU3_EINVAL, "extent n^%d=%d: the checkerboard needs even extents >= 2", i + 1, c->dims[i]);
+    V *= c->dims[i];
+    const int p = c->rng_period[i];
+    if (p != 0 && (p < 2 || (p & 1) || c->dims[i] % p))
+      return fail(SU3_EINVAL, "rng_period[%d]=%d must be even and divide n^%d=%d", i, p, i + 1, c->dims[i]);
+  }
+  const int layers = c->boundary == SU3_DLT ? 2 : 1;
+  if (c->boundary != SU3_PBC && c->boundary != SU3_DLT) return fail(SU3_EINVAL, "unknown boundary %d", c->boundary);
+  if (V * layers * 4 > 0x7fffffffLL) return fail(SU3_EINVAL, "lattice too large for 32-bit site keys");
+  if (!(c->beta >= 0.0) || !std::isfinite(c->beta)) return fail(SU3_EINVAL, "beta=%g must be finite and >= 0", c->beta);
+  if (c->hits < 1 || c->hits > 254) return fail(SU3_EINVAL, "hits=%d outside 1..254", c->hits);
+  if (c->storage != SU3_FP64_18 && c->storage != SU3_FP32_12) return fail(SU3_EINVAL, "unknown storage %d", c->storage);
+  if (c->start != SU3_START_COLD && c->start != SU3_START_HOT) return fail(SU3_EINVAL, "unknown start %d", c->start);
+  if (c->reunit_every < 0 || c->measure_every < 0 || c->measure_capacity < 0)
+    return fail(SU3_EINVAL, "negative cadence or capacity");
+  if (c->glue_mask < 0 || c->glue_mask >= (1 << c->D)) return fail(SU3_EINVAL, "glue_mask=%d out of range", c->glue_mask);
+  return SU3_OK;
+}
+
+static int nq_of(int storage) { return storage == SU3_FP64_18 ? 9 : 3; }
+
+static size_t link_bytes_of(const su3_config *c) {
+  size_t V = 1;
+  for (int i = 0; i < c->D; ++i) V *= (size_t)c->dims[i];
+  const int layers = c->boundary == SU3_DLT ? 2 : 1;
+  return (size_t)layers * c->D * V * nq_of(c->storage) * 16;
+}
+
+extern "C" size_t su3_link_bytes(const su3_config *c) {
+  std::string saved = g_err;
+  if (validate(c) != SU3_OK) return 0;
+  g_err = saved;
+  return link_bytes_of(c);
+}
+
+// ------------------------------------------------------------------ chains and the engine
+
+static int g_nsm = 0;
+
+static su3_status device_sm_count(int *nsm) {
+  if (!g_nsm) {
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  *nsm = g_nsm;
+  return SU3_OK;
+}
+
+struct Chain {
+  su3_config cfg{};
+  ChainDesc desc{};
+  ChainState state{};
+  void *links = nullptr;
+  bool own_links = false;
+  double *results = nullptr;
+  double *partials = nullptr;
+  unsigned long long *counters = nullptr;
+  size_t link_bytes = 0;
+  size_t bytes_total = 0;  // device bytes held (links if owned + scratch)
+  uint64_t job_id = 0;     // server only
+};
+
+static void fill_desc(Chain &ch, int tile) {
+  const su3_config &c = ch.cfg;
+  ChainDesc &d = ch.desc;
+  d.links = ch.links;
+  d.results = ch.results;
+  d.partials = ch.partials;
+  d.counters = ch.counters;
+  d.seed_lo = (uint32_t)(c.seed & 0xffffffffu);
+  d.seed_hi = (uint32_t)(c.seed >> 32);
+  d.D = c.D;
+  d.nlayers = c.boundary == SU3_DLT ? 2 : 1;
+  d.glue_mask = c.boundary == SU3_DLT ? (c.glue_mask ? c.glue_mask : (1 << c.D) - 1) : 0;
+  d.layer_blind = c.layer_blind ? 1 : 0;
+  d.custom_period = 0;
+  int V = 1, Vp = 1;
+  for (int i = 0; i < kMaxD; ++i) {
+    if (i < c.D) {
+      d.dims[i] = c.dims[i];
+      d.period[i] = c.rng_period[i] ? c.rng_period[i] : c.dims[i];
+      if (d.period[i] != d.dims[i]) d.custom_period = 1;
+      d.stride[i] = V;
+      d.pstride[i] = Vp;
+      V *= c.dims[i];
+      Vp *= d.period[i];
+    } else {
+      d.dims[i] = 1;
+      d.period[i] = 1;
+      d.stride[i] = V;
+      d.pstride[i] = Vp;
+    }
+  }
+  d.V = V;
+  d.Vh = V / 2;
+  d.Vp = Vp;
+  d.hits = c.hits;
+  d.reunit_every = c.reunit_every;
+  d.measure_every = c.measure_every;
+  d.tiles_per_layer = (d.Vh + tile - 1) / tile;
+  d.result_cap = c.measure_capacity > 0 ? c.measure_capacity : 1024;
+  d.spatial_per_layer = V / c.dims[c.D - 1];
+  d.beta_f = (float)c.beta;
+  d.beta_d = c.beta;
+}
+
+struct Engine {
+  int storage = SU3_FP64_18;
+  cudaStream_t stream = nullptr;
+  std::vector<Chain> chains;
+  // device mirrors
+  ChainDesc *d_desc = nullptr;
+  ChainState *d_state = nullptr;
+  EngineHeader *d_hdr = nullptr;
+  int32_t *d_tile_chain = nullptr;
+  size_t tile_cap = 0, chain_cap = 0;
+  double *d_meas_out = nullptr;  // stand-alone measurement results
+  double *h_pinned = nullptr;    // small pinned staging (results, counters)
+  int block = 128;
+  int ctas_per_sm = 0;
+  int total_tiles = 0;
+  bool use_graph = true;
+  cudaGraphExec_t graph = nullptr;
+  int graph_ticks = 0;
+  bool tiles_dirty = true;
+  // kernel timing (su3_set_profiling)
+  bool profiling = false;
+  struct EvPair {
+    cudaEvent_t a, b;
+    int kind;
+  };
+  std::vector<EvPair> prof_pending;
+  double prof_ms[3] = {0, 0, 0};
+  long long prof_n[3] = {0, 0, 0};
+
+  ~Engine() { release(); }
+
+  void drop_events() {
+    for (auto &p : prof_pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    prof_pending.clear();
+  }
+
+  // Ticks one by one, each between two events, classified by chain 0's stage.
+  su3_status profiled_ticks(long long n) {
+    if (tiles_dirty) TRY(rebuild());
+    int grid = 0;
+    TRY(grid_size(&grid));
+    ChainState s = chains[0].state;
+    const ChainDesc &d = chains[0].desc;
+    for (long long t = 0; t < n; ++t) {
+      EvPair p;
+      p.kind = s.stage < 2 * d.D ? 0 : (s.stage == kStageReunit ? 1 : 2);
+      CU(cudaEventCreate(&p.a));
+      CU(cudaEventCreate(&p.b));
+      CU(cudaEventRecord(p.a, stream));
+      CU(launch_tick(storage, args(), grid, block, stream));
+      CU(cudaEventRecord(p.b, stream));
+      prof_pending.push_back(p);
+      if (s.active) {
+        if (s.stage == kStageMeasure) s.n_meas += 1;
+        host_advance_stage(d, s);
+      }
+    }
+    return SU3_OK;
+  }
+
+  su3_status read_profile(su3_profile *out, int reset) {
+    CU(cudaStreamSynchronize(stream));
+    for (auto &p : prof_pending) {
+      float ms = 0;
+      CU(cudaEventElapsedTime(&ms, p.a, p.b));
+      prof_ms[p.kind] += ms;
+      prof_n[p.kind] += 1;
+    }
+    drop_events();
+    if (out) {
+      out->update_ms = prof_ms[0];
+      out->update_launches = prof_n[0];
+      out->reunit_ms = prof_ms[1];
+      out->reunit_launches = prof_n[1];
+      out->measure_ms = prof_ms[2];
+      out->measure_launches = prof_n[2];
+    }
+    if (reset)
+      for (int k = 0; k < 3; ++k) prof_ms[k] = 0, prof_n[k] = 0;
+    return SU3_OK;
+  }
+
+  void release() {
+    if (stream) cudaStreamSynchronize(stream);
+    drop_events();
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    for (auto &ch : chains) free_chain(ch);
+    chains.clear();
+    cudaFree(d_desc);
+    cudaFree(d_state);
+    cudaFree(d_hdr);
+    cudaFree(d_tile_chain);
+    cudaFree(d_meas_out);
+    cudaFreeHost(h_pinned);
+    d_desc = nullptr;
+    d_state = nullptr;
+    d_hdr = nullptr;
+    d_tile_chain = nullptr;
+    d_meas_out = nullptr;
+    h_pinned = nullptr;
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+    own_stream = false;
+  }
+
+  static void free_chain(Chain &ch) {
+    if (ch.own_links) cudaFree(ch.links);
+    cudaFree(ch.results);
+    cudaFree(ch.partials);
+    cudaFree(ch.counters);
+    ch.links = nullptr;
+    ch.results = ch.partials = nullptr;
+    ch.counters = nullptr;
+  }
+
+  bool own_stream = false;
+
+  su3_status init(int storage_, cudaStream_t st) {
+    storage = storage_;
+    stream = st;
+    if (!stream) {  // the legacy default stream cannot be captured into a graph
+      CU(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+      own_stream = true;
+    }
+    CU(cudaMalloc(&d_hdr, sizeof(EngineHeader)));
+    CU(cudaMemsetAsync(d_hdr, 0, sizeof(EngineHeader), stream));
+    CU(cudaMallocHost(&h_pinned, 4096));
+    return SU3_OK;
+  }
+
+  // Allocate a chain's memory and write its start configuration.
+  su3_status add_chain(const su3_config &cfg, Chain &out) {
+    Chain ch;
+    ch.cfg = cfg;
+    ch.link_bytes = link_bytes_of(&cfg);
+    if (cfg.link_buffer) {
+      if (cfg.link_buffer_bytes < ch.link_bytes)
+        return fail(SU3_EINVAL, "link_buffer holds %zu bytes, %zu needed", cfg.link_buffer_bytes, ch.link_bytes);
+      if (((uintptr_t)cfg.link_buffer) & 15) return fail(SU3_EINVAL, "link_buffer must be 16-byte aligned");
+      ch.links = cfg.link_buffer;
+      ch.own_links = false;
+    } else {
+      cudaError_t e = cudaMalloc(&ch.links, ch.link_bytes);
+      if (e != cudaSuccess) return fail(SU3_ENOMEM, "cudaMalloc of %zu link bytes: %s", ch.link_bytes, cudaGetErrorString(e));
+      ch.own_links = true;
+      ch.bytes_total += ch.link_bytes;
+    }
+    fill_desc(ch, 32);  // partials sized for the narrowest tile
+    const size_t npart = (size_t)ch.desc.nlayers * ch.desc.tiles_per_layer * kPartVals;
+    const size_t nres = (size_t)ch.desc.result_cap * (ch.desc.nlayers + 1) * kMeasVals;
+    cudaError_t e1 = cudaMalloc(&ch.partials, npart * sizeof(double));
+    cudaError_t e2 = cudaMalloc(&ch.results, nres * sizeof(double));
+    cudaError_t e3 = cudaMalloc(&ch.counters, 2 * sizeof(unsigned long long));
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+      free_chain(ch);
+      return fail(SU3_ENOMEM, "scratch allocation failed");
+    }
+    ch.bytes_total += npart * sizeof(double) + nres * sizeof(double) + 16;
+    CU(cudaMemsetAsync(ch.counters, 0, 2 * sizeof(unsigned long long), stream));
+    CU(cudaMemsetAsync(ch.results, 0, nres * sizeof(double), stream));
+    fill_desc(ch, block);
+    ch.state = ChainState{};
+    ch.state.active = 0;
+    out = ch;
+    return SU3_OK;
+  }
+
+  // Write a chain's start configuration through a scratch descriptor.
+  su3_status start_chain(Chain &ch) {
+    ChainDesc *dd = nullptr;
+    CU(cudaMallocAsync(&dd, sizeof(ChainDesc), stream));
+    CU(cudaMemcpyAsync(dd, &ch.desc, sizeof(ChainDesc), cudaMemcpyHostToDevice, stream));
+    const size_t nlinks = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
+    CU(launch_start(storage, dd, nlinks, ch.cfg.start == SU3_START_HOT, stream));
+    CU(cudaFreeAsync(dd, stream));
+    CU(cudaStreamSynchronize(stream));  // the host ChainDesc copy is freed with it
+    return SU3_OK;
+  }
+
+  // Rebuild tile bases and the tile -> chain map; upload descriptors.
+  su3_status rebuild() {
+    int tiles = 0;
+    for (auto &ch : chains) {
+      fill_desc(ch, block);
+      ch.desc.tile_base = tiles;
+      tiles += ch.desc.nlayers * ch.desc.tiles_per_layer;
+    }
+    total_tiles = tiles;
+    if (chains.size() > chain_cap) {
+      cudaFree(d_desc);
+      cudaFree(d_state);
+      chain_cap = std::max<size_t>(chains.size(), 2 * chain_cap);
+      CU(cudaMalloc(&d_desc, chain_cap * sizeof(ChainDesc)));
+      CU(cudaMalloc(&d_state, chain_cap * sizeof(ChainState)));
+      drop_graph();
+    }
+    if ((size_t)tiles > tile_cap) {
+      cudaFree(d_tile_chain);
+      tile_cap = std::max<size_t>(tiles, 2 * tile_cap);
+      CU(cudaMalloc(&d_tile_chain, tile_cap * sizeof(int32_t)));
+      drop_graph();
+    }
+    std::vector<int32_t> map(tiles);
+    std::vector<ChainDesc> descs(chains.size());
+    std::vector<ChainState> states(chains.size());
+    for (size_t c = 0; c < chains.size(); ++c) {
+      const ChainDesc &d = chains[c].desc;
+      for (int t = 0; t < d.nlayers * d.tiles_per_layer; ++t) map[d.tile_base + t] = (int32_t)c;
+      descs[c] = d;
+      states[c] = chains[c].state;
+    }
+    EngineHeader h{};
+    h.nchains = (int32_t)chains.size();
+    h.total_tiles = tiles;
+    h.tile = block;
+    h.done_ctas = 0;
+    // Pageable copies are staged by the driver before the call returns.
+    if (tiles) CU(cudaMemcpyAsync(d_tile_chain, map.data(), tiles * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    if (!chains.empty()) {
+      CU(cudaMemcpyAsync(d_desc, descs.data(), descs.size() * sizeof(ChainDesc), cudaMemcpyHostToDevice, stream));
+      CU(cudaMemcpyAsync(d_state, states.data(), states.size() * sizeof(ChainState), cudaMemcpyHostToDevice, stream));
+    }
+    CU(cudaMemcpyAsync(d_hdr, &h, sizeof h, cudaMemcpyHostToDevice, stream));
+    CU(cudaStreamSynchronize(stream));
+    tiles_dirty = false;
+    return SU3_OK;
+  }
+
+  su3_status upload_states() {
+    std::vector<ChainState> states(chains.size());
+    for (size_t c = 0; c < chains.size(); ++c) states[c] = chains[c].state;
+    if (!states.empty())
+      CU(cudaMemcpyAsync(d_state, states.data(), states.size() * sizeof(ChainState), cudaMemcpyHostToDevice, stream));
+    CU(cudaStreamSynchronize(stream));
+    return SU3_OK;
+  }
+
+  su3_status download_states() {
+    std::vector<ChainState> states(chains.size());
+    if (!states.empty())
+      CU(cudaMemcpyAsync(states.data(), d_state, states.size() * sizeof(ChainState), cudaMemcpyDeviceToHost, stream));
+    CU(cudaStreamSynchronize(stream));
+    for (size_t c = 0; c < chains.size(); ++c) chains[c].state = states[c];
+    return SU3_OK;
+  }
+
+  su3_status upload_desc(size_t c) {
+    CU(cudaMemcpyAsync(d_desc + c, &chains[c].desc, sizeof(ChainDesc), cudaMemcpyHostToDevice, stream));
+    CU(cudaStreamSynchronize(stream));
+    return SU3_OK;
+  }
+
+  void drop_graph() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    graph_ticks = 0;
+  }
+
+  su3_status grid_size(int *grid) {
+    int nsm = 0;
+    TRY(device_sm_count(&nsm));
+    int occ = ctas_per_sm;
+    if (occ <= 0) {
+      CU(tick_occupancy(storage, block, &occ));
+      if (occ < 1) occ = 1;
+    }
+    *grid = std::max(1, std::min(total_tiles, nsm * occ));
+    return SU3_OK;
+  }
+
+  EngineArgs args() const { return EngineArgs{d_desc, d_state, d_hdr, d_tile_chain}; }
+
+  su3_status tick_direct(int n) {
+    int grid = 0;
+    TRY(grid_size(&grid));
+    for (int i = 0; i < n; ++i) CU(launch_tick(storage, args(), grid, block, stream));
+    return SU3_OK;
+  }
+
+  static constexpr int kGraphTicks = 16;
+
+  su3_status ensure_graph() {
+    if (graph) return SU3_OK;
+    int grid = 0;
+    TRY(grid_size(&grid));
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < kGraphTicks; ++i) {
+      cudaError_t e = launch_tick(storage, args(), grid, block, stream);
+      if (e != cudaSuccess) {
+        cudaStreamEndCapture(stream, &g);
+        if (g) cudaGraphDestroy(g);
+        return fail(SU3_ECUDA, "launch during capture: %s", cudaGetErrorString(e));
+      }
+    }
+    CU(cudaStreamEndCapture(stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(SU3_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    graph_ticks = kGraphTicks;
+    return SU3_OK;
+  }
+
+  // Launch n ticks: whole graphs, then single launches for the remainder.
+  su3_status run_ticks(long long n) {
+    if (n <= 0) return SU3_OK;
+    if (tiles_dirty) TRY(rebuild());
+    if (total_tiles == 0) return SU3_OK;
+    if (use_graph) {
+      TRY(ensure_graph());
+      while (n >= graph_ticks) {
+        CU(cudaGraphLaunch(graph, stream));
+        n -= graph_ticks;
+      }
+    }
+    return tick_direct((int)n);
+  }
+
+  // Host mirror: ticks until every chain in `which` is idle again.
+  long long ticks_to_finish() {
+    long long most = 0;
+    for (auto &ch : chains) {
+      ChainState s = ch.state;
+      long long t = 0;
+      while (s.active) {
+        if (s.stage == kStageMeasure) s.n_meas += 1;
+        host_advance_stage(ch.desc, s);
+        ++t;
+      }
+      most = std::max(most, t);
+    }
+    return most;
+  }
+
+  // Advance the host mirror of every chain by n ticks.
+  void mirror_ticks(long long n) {
+    for (auto &ch : chains)
+      for (long long t = 0; t < n && ch.state.active; ++t) {
+        if (ch.state.stage == kStageMeasure) ch.state.n_meas += 1;
+        host_advance_stage(ch.desc, ch.state);
+      }
+  }
+
+  su3_status sweep_all(int n) {
+    if (n < 0) return fail(SU3_EINVAL, "negative sweep count %d", n);
+    if (n == 0) return SU3_OK;
+    if (tiles_dirty) TRY(rebuild());
+    for (auto &ch : chains) {
+      ch.state.target = ch.state.sweep + (uint32_t)n;
+      ch.state.active = 1;
+    }
+    TRY(upload_states());
+    const long long T = ticks_to_finish();
+    TRY(profiling ? profiled_ticks(T) : run_ticks(T));
+    mirror_ticks(T);
+    return SU3_OK;
+  }
+
+  su3_status measure_chain(size_t c, double *host_out /* 5*(layers+1) */) {
+    if (tiles_dirty) TRY(rebuild());
+    Chain &ch = chains[c];
+    const int nvals = (ch.desc.nlayers + 1) * kMeasVals;
+    if (!d_meas_out) CU(cudaMalloc(&d_meas_out, 3 * kMeasVals * sizeof(double)));
+    CU(launch_measure(storage, d_desc + c, ch.desc.nlayers * ch.desc.tiles_per_layer, block, d_meas_out, stream));
+    CU(cudaMemcpyAsync(h_pinned, d_meas_out, nvals * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CU(cudaStreamSynchronize(stream));
+    std::memcpy(host_out, h_pinned, nvals * sizeof(double));
+    return SU3_OK;
+  }
+
+  su3_status get_links(size_t c, double *host, size_t n) {
+    if (tiles_dirty) TRY(rebuild());
+    Chain &ch = chains[c];
+    const size_t nlinks = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
+    if (!host || n < nlinks * 18) return fail(SU3_EINVAL, "host buffer holds %zu doubles, %zu needed", n, nlinks * 18);
+    double *canon = nullptr;
+    CU(cudaMallocAsync(&canon, nlinks * 18 * sizeof(double), stream));
+    CU(launch_convert(storage, d_desc + c, nlinks, canon, 1, stream));
+    CU(cudaMemcpyAsync(host, canon, nlinks * 18 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CU(cudaFreeAsync(canon, stream));
+    CU(cudaStreamSynchronize(stream));
+    return SU3_OK;
+  }
+
+  su3_status set_links(size_t c, const double *host, size_t n) {
+    if (tiles_dirty) TRY(rebuild());
+    Chain &ch = chains[c];
+    const size_t nlinks = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
+    if (!host || n < nlinks * 18) return fail(SU3_EINVAL, "host buffer holds %zu doubles, %zu needed", n, nlinks * 18);
+    double *canon = nullptr;
+    CU(cudaMallocAsync(&canon, nlinks * 18 * sizeof(double), stream));
+    CU(cudaMemcpyAsync(canon, host, nlinks * 18 * sizeof(double), cudaMemcpyHostToDevice, stream));
+    CU(launch_convert(storage, d_desc + c, nlinks, canon, 0, stream));
+    CU(cudaFreeAsync(canon, stream));
+    CU(cudaStreamSynchronize(stream));
+    return SU3_OK;
+  }
+
+  su3_status counters(size_t c, uint64_t *prop, uint64_t *acc) {
+    CU(cudaMemcpyAsync(h_pinned, chains[c].counters, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
+    CU(cudaStreamSynchronize(stream));
+    unsigned long long v[2];
+    std::memcpy(v, h_pinned, sizeof v);
+    if (prop) *prop = v[0];
+    if (acc) *acc = v[1];
+    return SU3_OK;
+  }
+
+  su3_status set_launch(int threads, int ctas) {
+    if (threads < 32 || threads > 256 || (threads & 31))
+      return fail(SU3_EINVAL, "threads=%d must be a multiple of 32 in 32..256", threads);
+    if (ctas < 0 || ctas > 64) return fail(SU3_EINVAL, "ctas_per_sm=%d outside 0..64", ctas);
+    CU(cudaStreamSynchronize(stream));
+    block = threads;
+    ctas_per_sm = ctas;
+    drop_graph();
+    tiles_dirty = true;
+    return SU3_OK;
+  }
+};
+
+// ------------------------------------------------------------------ lattice handle
+
+struct su3_lattice {
+  Engine eng;
+};
+
+static su3_status make_lattice(const su3_config *cfg, su3_lattice **out) {
+  if (!out) return fail(SU3_EINVAL, "out is NULL");
+  *out = nullptr;
+  TRY(validate(cfg));
+  auto *lat = new su3_lattice();
+  su3_status st = lat->eng.init(cfg->storage, (cudaStream_t)cfg->stream);
+  if (st == SU3_OK) {
+    Chain ch;
+    st = lat->eng.add_chain(*cfg, ch);
+    if (st == SU3_OK) {
+      lat->eng.chains.push_back(ch);
+      st = lat->eng.start_chain(lat->eng.chains.back());
+    }
+    if (st == SU3_OK) st = lat->eng.rebuild();
+  }
+  if (st != SU3_OK) {
+    std::string msg = g_err;
+    delete lat;
+    g_err = msg;
+    return st;
+  }
+  *out = lat;
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_lattice_create_ex(const su3_config *cfg, su3_lattice **out) { return make_lattice(cfg, out); }
+
+extern "C" su3_status su3_lattice_create(int D, const int *dims, su3_boundary boundary, double beta, uint64_t seed,
+                                         su3_lattice **out) {
+  su3_config c;
+  su3_config_init(&c);
+  if (!dims) return fail(SU3_EINVAL, "dims is NULL");
+  if (D < 2 || D > SU3_MAX_D) return fail(SU3_EINVAL, "D=%d outside 2..%d", D, SU3_MAX_D);
+  c.D = D;
+  for (int i = 0; i < D; ++i) c.dims[i] = dims[i];
+  c.boundary = boundary;
+  c.beta = beta;
+  c.seed = seed;
+  return make_lattice(&c, out);
+}
+
+extern "C" void su3_lattice_destroy(su3_lattice *lat) { delete lat; }
+
+#define LAT_CHECK(lat) \
+  if (!(lat)) return fail(SU3_EINVAL, "lattice handle is NULL")
+
+extern "C" su3_status su3_sweep(su3_lattice *lat, int n, int hits) {
+  LAT_CHECK(lat);
+  if (hits < 1 || hits > 254) return fail(SU3_EINVAL, "hits=%d outside 1..254", hits);
+  Chain &ch = lat->eng.chains[0];
+  if (ch.cfg.hits != hits) {
+    ch.cfg.hits = hits;
+    ch.desc.hits = hits;
+    TRY(lat->eng.upload_desc(0));
+  }
+  return lat->eng.sweep_all(n);
+}
+
+extern "C" su3_status su3_reunitarize(su3_lattice *lat) {
+  LAT_CHECK(lat);
+  Engine &e = lat->eng;
+  if (e.tiles_dirty) TRY(e.rebuild());
+  Chain &ch = e.chains[0];
+  // one re-unitarisation stage through the tick kernel
+  const ChainState saved = ch.state;
+  ch.state.stage = kStageReunit;
+  ch.state.active = 1;
+  ch.state.target = ch.state.sweep;  // idle again right after
+  TRY(e.upload_states());
+  TRY(e.tick_direct(1));
+  ch.state = saved;
+  ch.state.stage = 0;
+  ch.state.active = 0;
+  return e.upload_states();
+}
+
+extern "C" su3_status su3_plaquette(su3_lattice *lat, int layer, double *total, double *space, double *time) {
+  LAT_CHECK(lat);
+  Chain &ch = lat->eng.chains[0];
+  if (layer < -1 || layer >= ch.desc.nlayers) return fail(SU3_EINVAL, "layer %d out of range", layer);
+  double v[3 * kMeasVals];
+  TRY(lat->eng.measure_chain(0, v));
+  const int slot = layer < 0 ? ch.desc.nlayers : layer;
+  if (total) *total = v[slot * kMeasVals + 0];
+  if (space) *space = v[slot * kMeasVals + 1];
+  if (time) *time = v[slot * kMeasVals + 2];
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_polyakov(su3_lattice *lat, int layer, double *re, double *im) {
+  LAT_CHECK(lat);
+  Chain &ch = lat->eng.chains[0];
+  if (layer < -1 || layer >= ch.desc.nlayers) return fail(SU3_EINVAL, "layer %d out of range", layer);
+  double v[3 * kMeasVals];
+  TRY(lat->eng.measure_chain(0, v));
+  const int slot = layer < 0 ? ch.desc.nlayers : layer;
+  if (re) *re = v[slot * kMeasVals + 3];
+  if (im) *im = v[slot * kMeasVals + 4];
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_measure_async(su3_lattice *lat, double *device_out) {
+  LAT_CHECK(lat);
+  if (!device_out) return fail(SU3_EINVAL, "device_out is NULL");
+  Engine &e = lat->eng;
+  if (e.tiles_dirty) TRY(e.rebuild());
+  Chain &ch = e.chains[0];
+  CU(launch_measure(e.storage, e.d_desc, ch.desc.nlayers * ch.desc.tiles_per_layer, e.block, device_out, e.stream));
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_measurements(su3_lattice *lat, double *host_out, size_t max, size_t *count) {
+  LAT_CHECK(lat);
+  Engine &e = lat->eng;
+  Chain &ch = e.chains[0];
+  const size_t per = (size_t)(ch.desc.nlayers + 1) * kMeasVals;
+  const uint32_t n = ch.state.n_meas;
+  const size_t cap = (size_t)ch.desc.result_cap;
+  const size_t avail = std::min<size_t>(n, cap);
+  const size_t take = std::min(avail, max);
+  std::vector<double> all(cap * per);
+  CU(cudaMemcpyAsync(all.data(), ch.results, cap * per * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  CU(cudaStreamSynchronize(e.stream));
+  const size_t first = n - avail;  // oldest kept
+  for (size_t i = 0; i < take; ++i) {
+    const size_t slot = (first + i) % cap;
+    std::memcpy(host_out + i * per, all.data() + slot * per, per * sizeof(double));
+  }
+  if (count) *count = take;
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_get_links(su3_lattice *lat, double *host, size_t n) {
+  LAT_CHECK(lat);
+  return lat->eng.get_links(0, host, n);
+}
+
+extern "C" su3_status su3_set_links(su3_lattice *lat, const double *host, size_t n) {
+  LAT_CHECK(lat);
+  return lat->eng.set_links(0, host, n);
+}
+
+extern "C" su3_status su3_stats(su3_lattice *lat, uint64_t *proposals, uint64_t *accepts, uint64_t *sweeps) {
+  LAT_CHECK(lat);
+  TRY(lat->eng.counters(0, proposals, accepts));
+  if (sweeps) *sweeps = lat->eng.chains[0].state.sweep;
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_set_sweep_counter(su3_lattice *lat, uint64_t sweeps) {
+  LAT_CHECK(lat);
+  if (sweeps > 0xffffffffull) return fail(SU3_EINVAL, "sweep counter is 32-bit");
+  Chain &ch = lat->eng.chains[0];
+  ch.state.sweep = (uint32_t)sweeps;
+  ch.state.stage = 0;
+  ch.state.active = 0;
+  return lat->eng.upload_states();
+}
+
+extern "C" su3_status su3_lattice_info(su3_lattice *lat, size_t *links, size_t *bytes) {
+  LAT_CHECK(lat);
+  const Chain &ch = lat->eng.chains[0];
+  if (links) *links = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
+  if (bytes) *bytes = ch.link_bytes;
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_set_launch(su3_lattice *lat, int threads, int ctas_per_sm) {
+  LAT_CHECK(lat);
+  return lat->eng.set_launch(threads, ctas_per_sm);
+}
+
+extern "C" su3_status su3_use_graph(su3_lattice *lat, int on) {
+  LAT_CHECK(lat);
+  CU(cudaStreamSynchronize(lat->eng.stream));
+  lat->eng.use_graph = on != 0;
+  lat->eng.drop_graph();
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_set_profiling(su3_lattice *lat, int on) {
+  LAT_CHECK(lat);
+  lat->eng.profiling = on != 0;
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_get_profile(su3_lattice *lat, su3_profile *out, int reset) {
+  LAT_CHECK(lat);
+  return lat->eng.read_profile(out, reset);
+}
+
+// Time candidate launch shapes on a scratch copy of the links (the lattice,
+// its counters and its stage machine are restored afterwards).
+static su3_status autotune_engine(Engine &e, int *threads, int *ctas, double *us) {
+  if (e.tiles_dirty) TRY(e.rebuild());
+  CU(cudaStreamSynchronize(e.stream));
+  std::vector<void *> backup(e.chains.size(), nullptr);
+  for (size_t c = 0; c < e.chains.size(); ++c) {
+    CU(cudaMalloc(&backup[c], e.chains[c].link_bytes));
+    CU(cudaMemcpyAsync(backup[c], e.chains[c].links, e.chains[c].link_bytes, cudaMemcpyDeviceToDevice, e.stream));
+  }
+  std::vector<ChainState> saved_state;
+  std::vector<unsigned long long> saved_cnt(2 * e.chains.size());
+  for (size_t c = 0; c < e.chains.size(); ++c) {
+    saved_state.push_back(e.chains[c].state);
+    CU(cudaMemcpyAsync(&saved_cnt[2 * c], e.chains[c].counters, 16, cudaMemcpyDeviceToHost, e.stream));
+  }
+  CU(cudaStreamSynchronize(e.stream));
+  const int saved_block = e.block, saved_ctas = e.ctas_per_sm;
+  const bool saved_graph = e.use_graph, saved_prof = e.profiling;
+  e.profiling = false;
+  std::vector<int> saved_meas;
+  for (auto &ch : e.chains) {
+    saved_meas.push_back(ch.cfg.measure_every);
+    ch.cfg.measure_every = 0;  // timing runs record no measurements
+  }
+  cudaEvent_t a, b;
+  CU(cudaEventCreate(&a));
+  CU(cudaEventCreate(&b));
+  double best = 1e30;
+  int best_t = saved_block, best_c = saved_ctas;
+  const int cand_t[] = {64, 128, 256};
+  su3_status st = SU3_OK;
+  for (int t : cand_t) {
+    int occ = 0;
+    if (tick_occupancy(e.storage, t, &occ) != cudaSuccess || occ < 1) continue;
+    for (int c = 1; c <= occ && st == SU3_OK; c = (c < occ && 2 * c > occ) ? occ : 2 * c) {
+      if ((st = e.set_launch(t, c)) != SU3_OK) break;
+      e.use_graph = true;
+      if ((st = e.sweep_all(1)) != SU3_OK) break;  // warm-up + graph capture
+      cudaEventRecord(a, e.stream);
+      const int reps = 3;
+      if ((st = e.sweep_all(reps)) != SU3_OK) break;
+      cudaEventRecord(b, e.stream);
+      cudaEventSynchronize(b);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      const double per = 1e3 * ms / reps;
+      if (per < best) {
+        best = per;
+        best_t = t;
+        best_c = c;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  for (size_t c = 0; c < e.chains.size(); ++c) {
+    e.chains[c].cfg.measure_every = saved_meas[c];
+    cudaMemcpyAsync(e.chains[c].links, backup[c], e.chains[c].link_bytes, cudaMemcpyDeviceToDevice, e.stream);
+    cudaMemcpyAsync(e.chains[c].counters, &saved_cnt[2 * c], 16, cudaMemcpyHostToDevice, e.stream);
+    e.chains[c].state = saved_state[c];
+  }
+  cudaStreamSynchronize(e.stream);
+  for (void *p : backup) cudaFree(p);
+  e.profiling = saved_prof;
+  if (st != SU3_OK) return st;
+  e.use_graph = saved_graph;
+  TRY(e.set_launch(best_t, best_c));
+  TRY(e.rebuild());
+  if (threads) *threads = best_t;
+  if (ctas) *ctas = best_c;
+  if (us) *us = best;
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_autotune(su3_lattice *lat, int *threads, int *ctas_per_sm, double *us_per_sweep) {
+  LAT_CHECK(lat);
+  return autotune_engine(lat->eng, threads, ctas_per_sm, us_per_sweep);
+}
+
+// ------------------------------------------------------------------ ensembles
+
+struct su3_ensemble {
+  Engine eng;
+};
+
+extern "C" su3_status su3_ensemble_create(const su3_config *cfgs, int nchains, void *stream, su3_ensemble **out) {
+  if (!out) return fail(SU3_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfgs || nchains < 1) return fail(SU3_EINVAL, "need at least one chain");
+  for (int c = 0; c < nchains; ++c) {
+    TRY(validate(&cfgs[c]));
+    if (cfgs[c].storage != cfgs[0].storage) return fail(SU3_EINVAL, "all chains of an ensemble share one storage");
+  }
+  auto *ens = new su3_ensemble();
+  su3_status st = ens->eng.init(cfgs[0].storage, (cudaStream_t)stream);
+  for (int c = 0; c < nchains && st == SU3_OK; ++c) {
+    su3_config cfg = cfgs[c];
+    cfg.stream = stream;
+    Chain ch;
+    st = ens->eng.add_chain(cfg, ch);
+    if (st == SU3_OK) {
+      ens->eng.chains.push_back(ch);
+      st = ens->eng.start_chain(ens->eng.chains.back());
+    }
+  }
+  if (st == SU3_OK) st = ens->eng.rebuild();
+  if (st != SU3_OK) {
+    std::string msg = g_err;
+    delete ens;
+    g_err = msg;
+    return st;
+  }
+  *out = ens;
+  return SU3_OK;
+}
+
+extern "C" void su3_ensemble_destroy(su3_ensemble *ens) { delete ens; }
+
+extern "C" su3_status su3_ensemble_sweep(su3_ensemble *ens, int n) {
+  if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
+  return ens->eng.sweep_all(n);
+}
+
+extern "C" su3_status su3_ensemble_measure(su3_ensemble *ens, double *host_out) {
+  if (!ens || !host_out) return fail(SU3_EINVAL, "NULL argument");
+  for (size_t c = 0; c < ens->eng.chains.size(); ++c) {
+    double v[3 * kMeasVals];
+    TRY(ens->eng.measure_chain(c, v));
+    const int slot = ens->eng.chains[c].desc.nlayers;
+    for (int k = 0; k < kMeasVals; ++k) host_out[kMeasVals * c + k] = v[slot * kMeasVals + k];
+  }
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_ensemble_get_links(su3_ensemble *ens, int chain, double *host, size_t n) {
+  if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
+  if (chain < 0 || (size_t)chain >= ens->eng.chains.size()) return fail(SU3_EINVAL, "chain %d out of range", chain);
+  return ens->eng.get_links((size_t)chain, host, n);
+}
+
+extern "C" su3_status su3_ensemble_set_launch(su3_ensemble *ens, int threads, int ctas_per_sm) {
+  if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
+  return ens->eng.set_launch(threads, ctas_per_sm);
+}
+
+extern "C" su3_status su3_ensemble_use_graph(su3_ensemble *ens, int on) {
+  if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
+  CU(cudaStreamSynchronize(ens->eng.stream));
+  ens->eng.use_graph = on != 0;
+  ens->eng.drop_graph();
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_ensemble_set_profiling(su3_ensemble *ens, int on) {
+  if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
+  ens->eng.profiling = on != 0;
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_ensemble_get_profile(su3_ensemble *ens, su3_profile *out, int reset) {
+  if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
+  return ens->eng.read_profile(out, reset);
+}
+
+// ------------------------------------------------------------------ job server
+
+struct ServerJob {
+  uint64_t id;
+  su3_job job;
+  double submit_s;
+};
+
+struct su3_server {
+  Engine eng;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<ServerJob> queue;
+  std::map<uint64_t, su3_result> finished;
+  std::map<uint64_t, int> running;  // id -> 1
+  std::map<uint64_t, double> start_time;
+  std::map<uint64_t, double> submit_time;
+  std::thread worker;
+  bool stop = false;
+  size_t budget = 0, used = 0;
+  int max_slots = 0;
+  uint64_t next_id = 1;
+  std::chrono::steady_clock::time_point t0;
+  std::string worker_error;
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  void loop();
+  su3_status admit_locked(std::vector<ServerJob> &admitted);
+};
+
+static size_t job_bytes(const su3_config &c) {
+  // links + measurement scratch (partials for 32-wide tiles, result ring, counters)
+  size_t V = 1;
+  for (int i = 0; i < c.D; ++i) V *= (size_t)c.dims[i];
+  const size_t layers = c.boundary == SU3_DLT ? 2 : 1;
+  const size_t tiles = layers * ((V / 2 + 31) / 32);
+  const size_t cap = c.measure_capacity > 0 ? (size_t)c.measure_capacity : 1024;
+  return link_bytes_of(&c) + tiles * kPartVals * 8 + cap * (layers + 1) * kMeasVals * 8 + 16;
+}
+
+extern "C" su3_status su3_server_create(size_t hbm_budget_bytes, int max_slots, su3_server **out) {
+  if (!out) return fail(SU3_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_slots < 1) return fail(SU3_EINVAL, "max_slots=%d < 1", max_slots);
+  auto *srv = new su3_server();
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete srv;
+    return fail(SU3_ECUDA, "cudaStreamCreate failed");
+  }
+  su3_status s = srv->eng.init(SU3_FP32_12, st);
+  if (s != SU3_OK) {
+    delete srv;
+    return s;
+  }
+  if (hbm_budget_bytes == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    hbm_budget_bytes = (size_t)(0.8 * (double)fr);
+  }
+  srv->budget = hbm_budget_bytes;
+  srv->max_slots = max_slots;
+  srv->t0 = std::chrono::steady_clock::now();
+  srv->worker = std::thread([srv] { srv->loop(); });
+  *out = srv;
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_server_submit(su3_server *srv, const su3_job *job, uint64_t *job_id) {
+  if (!srv || !job) return fail(SU3_EINVAL, "NULL argument");
+  su3_config c = job->cfg;
+  c.stream = nullptr;
+  c.link_buffer = nullptr;
+  c.link_buffer_bytes = 0;
+  c.storage = SU3_FP32_12;
+  TRY(validate(&c));
+  if (job->sweeps < 1) return fail(SU3_EINVAL, "sweeps=%d < 1", job->sweeps);
+  if (job_bytes(c) > srv->budget) return fail(SU3_ENOMEM, "job needs %zu bytes, budget is %zu", job_bytes(c), srv->budget);
+  std::lock_guard<std::mutex> lk(srv->mu);
+  ServerJob sj{srv->next_id++, *job, srv->now()};
+  sj.job.cfg = c;
+  srv->queue.push_back(sj);
+  srv->submit_time[sj.id] = sj.submit_s;
+  if (job_id) *job_id = sj.id;
+  srv->cv.notify_all();
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_server_poll(su3_server *srv, uint64_t job_id, su3_result *out) {
+  if (!srv) return fail(SU3_EINVAL, "server handle is NULL");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->finished.find(job_id);
+  if (it != srv->finished.end()) {
+    if (out) *out = it->second;
+    srv->finished.erase(it);
+    return SU3_OK;
+  }
+  if (srv->submit_time.count(job_id)) return SU3_EBUSY;
+  return fail(SU3_ENOTFOUND, "job %llu unknown or already collected", (unsigned long long)job_id);
+}
+
+extern "C" su3_status su3_server_wait(su3_server *srv, uint64_t job_id, double timeout_s, su3_result *out) {
+  if (!srv) return fail(SU3_EINVAL, "server handle is NULL");
+  std::unique_lock<std::mutex> lk(srv->mu);
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+  while (true) {
+    auto it = srv->finished.find(job_id);
+    if (it != srv->finished.end()) {
+      if (out) *out = it->second;
+      srv->finished.erase(it);
+      return SU3_OK;
+    }
+    if (!srv->submit_time.count(job_id))
+      return fail(SU3_ENOTFOUND, "job %llu unknown or already collected", (unsigned long long)job_id);
+    if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout && !srv->finished.count(job_id))
+      return fail(SU3_ETIMEOUT, "job %llu not finished after %g s", (unsigned long long)job_id, timeout_s);
+  }
+}
+
+extern "C" su3_status su3_server_load(su3_server *srv, int *queued, int *resident, int *finished) {
+  if (!srv) return fail(SU3_EINVAL, "server handle is NULL");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (queued) *queued = (int)srv->queue.size();
+  if (resident) *resident = (int)srv->running.size();
+  if (finished) *finished = (int)srv->finished.size();
+  return SU3_OK;
+}
+
+extern "C" void su3_server_destroy(su3_server *srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+    srv->cv.notify_all();
+  }
+  if (srv->worker.joinable()) srv->worker.join();
+  cudaStream_t st = srv->eng.stream;
+  srv->eng.release();
+  if (st) cudaStreamDestroy(st);
+  delete srv;
+}
+
+// Admit queued jobs in arrival order while a slot and budget are free.
+su3_status su3_server::admit_locked(std::vector<ServerJob> &admitted) {
+  while (!queue.empty() && (int)(running.size() + admitted.size()) < max_slots) {
+    const ServerJob &j = queue.front();
+    const size_t need = job_bytes(j.job.cfg);
+    if (used + need > budget) break;  // first-come first-served: wait for memory
+    used += need;
+    admitted.push_back(j);
+    queue.pop_front();
+  }
+  return SU3_OK;
+}
+
+void su3_server::loop() {
+  const long long kTicksPerRound = Engine::kGraphTicks;
+  while (true) {
+    std::vector<ServerJob> admitted;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      while (!stop && queue.empty() && eng.chains.empty()) cv.wait(lk);
+      if (stop) break;
+      admit_locked(admitted);
+    }
+    // Bring admitted jobs on the device (outside the lock).
+    bool changed = false;
+    for (auto &j : admitted) {
+      Chain ch;
+      su3_config c = j.job.cfg;
+      c.stream = eng.stream;
+      su3_status st = eng.add_chain(c, ch);
+      if (st == SU3_OK) {
+        eng.chains.push_back(ch);
+        st = eng.start_chain(eng.chains.back());
+        if (st != SU3_OK) {
+          Engine::free_chain(eng.chains.back());
+          eng.chains.pop_back();
+        }
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      if (st != SU3_OK) {
+        su3_result r{};
+        r.job_id = j.id;
+        r.status = st;
+        r.submit_s = j.submit_s;
+        r.start_s = r.finish_s = now();
+        finished[j.id] = r;
+        used -= job_bytes(j.job.cfg);
+        cv.notify_all();
+        continue;
+      }
+      Chain &nc = eng.chains.back();
+      nc.job_id = j.id;
+      nc.state.sweep = 0;
+      nc.state.stage = 0;
+      nc.state.target = (uint32_t)j.job.sweeps;
+      nc.state.active = 1;
+      running[j.id] = 1;
+      start_time[j.id] = now();
+      changed = true;
+    }
+    if (changed || eng.tiles_dirty) {
+      if (eng.rebuild() != SU3_OK) {
+        worker_error = g_err;
+        break;
+      }
+    }
+    if (eng.chains.empty()) continue;
+    // One round of fused ticks for every resident chain.
+    if (eng.run_ticks(kTicksPerRound) != SU3_OK || eng.download_states() != SU3_OK) {
+      worker_error = g_err;
+      break;
+    }
+    // Retire finished chains: measure all of them while the device
+    // descriptors still match the host order, then release in reverse.
+    std::vector<size_t> done;
+    for (size_t c = 0; c < eng.chains.size(); ++c)
+      if (!eng.chains[c].state.active) done.push_back(c);
+    bool retired = !done.empty();
+    std::vector<su3_result> results;
+    for (size_t c : done) {
+      Chain &ch = eng.chains[c];
+      su3_result r{};
+      r.job_id = ch.job_id;
+      r.status = SU3_OK;
+      r.nlayers = ch.desc.nlayers;
+      double v[3 * kMeasVals];
+      if (eng.measure_chain(c, v) == SU3_OK) {
+        const int w = ch.desc.nlayers;
+        for (int k = 0; k < 3; ++k) r.plaquette[k] = v[w * kMeasVals + k];
+        r.polyakov[0] = v[w * kMeasVals + 3];
+        r.polyakov[1] = v[w * kMeasVals + 4];
+        for (int l = 0; l < ch.desc.nlayers; ++l) r.layer_plaquette[l] = v[l * kMeasVals];
+      } else {
+        r.status = SU3_ECUDA;
+      }
+      eng.counters(c, &r.proposals, &r.accepts);
+      results.push_back(r);
+    }
+    std::vector<size_t> bytes(done.size());
+    for (size_t i = done.size(); i-- > 0;) {
+      Chain &ch = eng.chains[done[i]];
+      bytes[i] = job_bytes(ch.cfg);
+      Engine::free_chain(ch);
+      eng.chains.erase(eng.chains.begin() + (long)done[i]);
+    }
+    if (retired) {
+      std::lock_guard<std::mutex> lk(mu);
+      for (size_t i = 0; i < results.size(); ++i) {
+        su3_result &r = results[i];
+        r.submit_s = submit_time[r.job_id];
+        r.start_s = start_time[r.job_id];
+        r.finish_s = now();
+        finished[r.job_id] = r;
+        running.erase(r.job_id);
+        start_time.erase(r.job_id);
+        used -= bytes[i];
+      }
+      cv.notify_all();
+    }
+    if (retired) eng.tiles_dirty = true;
+  }
+  // Jobs left behind end with EBUSY.
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto &ch : eng.chains) {
+    su3_result r{};
+    r.job_id = ch.job_id;
+    r.status = SU3_EBUSY;
+    finished[ch.job_id] = r;
+  }
+  for (auto &j : queue) {
+    su3_result r{};
+    r.job_id = j.id;
+    r.status = SU3_EBUSY;
+    finished[j.id] = r;
+  }
+  queue.clear();
+  cv.notify_all();
+}

@@ -1,0 +1,383 @@
+// su3_device.cuh -- device arithmetic for the checkerboard SU(3) heatbath:
+// complex 3x3 algebra, link storage formats, Philox4x32-10, the
+// Kennedy-Pendleton SU(2) draw and the Cabibbo-Marinari link update.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "su3_engine.h"
+
+namespace su3g {
+
+// ------------------------------------------------------------------ complex 3x3
+
+template <typename R>
+struct C {
+  R re, im;
+};
+
+template <typename R>
+struct M3 {
+  C<R> e[3][3];
+};
+
+template <typename R>
+__device__ __forceinline__ M3<R> m3_zero() {
+  M3<R> m;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) m.e[i][j] = {R(0), R(0)};
+  return m;
+}
+
+// c = a b
+template <typename R>
+__device__ __forceinline__ M3<R> mul_nn(const M3<R> &a, const M3<R> &b) {
+  M3<R> c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R re = a.e[i][0].re * b.e[0][j].re - a.e[i][0].im * b.e[0][j].im;
+      R im = a.e[i][0].re * b.e[0][j].im + a.e[i][0].im * b.e[0][j].re;
+#pragma unroll
+      for (int k = 1; k < 3; ++k) {
+        re += a.e[i][k].re * b.e[k][j].re - a.e[i][k].im * b.e[k][j].im;
+        im += a.e[i][k].re * b.e[k][j].im + a.e[i][k].im * b.e[k][j].re;
+      }
+      c.e[i][j] = {re, im};
+    }
+  return c;
+}
+
+// c = a b^+
+template <typename R>
+__device__ __forceinline__ M3<R> mul_nd(const M3<R> &a, const M3<R> &b) {
+  M3<R> c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R re = a.e[i][0].re * b.e[j][0].re + a.e[i][0].im * b.e[j][0].im;
+      R im = a.e[i][0].im * b.e[j][0].re - a.e[i][0].re * b.e[j][0].im;
+#pragma unroll
+      for (int k = 1; k < 3; ++k) {
+        re += a.e[i][k].re * b.e[j][k].re + a.e[i][k].im * b.e[j][k].im;
+        im += a.e[i][k].im * b.e[j][k].re - a.e[i][k].re * b.e[j][k].im;
+      }
+      c.e[i][j] = {re, im};
+    }
+  return c;
+}
+
+// c = a^+ b
+template <typename R>
+__device__ __forceinline__ M3<R> mul_dn(const M3<R> &a, const M3<R> &b) {
+  M3<R> c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R re = a.e[0][i].re * b.e[0][j].re + a.e[0][i].im * b.e[0][j].im;
+      R im = a.e[0][i].re * b.e[0][j].im - a.e[0][i].im * b.e[0][j].re;
+#pragma unroll
+      for (int k = 1; k < 3; ++k) {
+        re += a.e[k][i].re * b.e[k][j].re + a.e[k][i].im * b.e[k][j].im;
+        im += a.e[k][i].re * b.e[k][j].im - a.e[k][i].im * b.e[k][j].re;
+      }
+      c.e[i][j] = {re, im};
+    }
+  return c;
+}
+
+template <typename R>
+__device__ __forceinline__ void m3_acc(M3<R> &a, const M3<R> &b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      a.e[i][j].re += b.e[i][j].re;
+      a.e[i][j].im += b.e[i][j].im;
+    }
+}
+
+// Re Tr(a b^+) = sum_ij Re(a_ij conj(b_ij))
+template <typename R>
+__device__ __forceinline__ R retr_nd(const M3<R> &a, const M3<R> &b) {
+  R s = R(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s += a.e[i][j].re * b.e[i][j].re + a.e[i][j].im * b.e[i][j].im;
+  return s;
+}
+
+// Third row of an SU(3) matrix from the first two: conj(row1 x row2).
+template <typename R>
+__device__ __forceinline__ void third_row(M3<R> &m) {
+  const C<R> *a = m.e[0], *b = m.e[1];
+  // (p q - r s)^* for the cross product components
+  auto cr = [](C<R> p, C<R> q, C<R> r, C<R> s) -> C<R> {
+    R re = p.re * q.re - p.im * q.im - (r.re * s.re - r.im * s.im);
+    R im = p.re * q.im + p.im * q.re - (r.re * s.im + r.im * s.re);
+    return {re, -im};
+  };
+  m.e[2][0] = cr(a[1], b[2], a[2], b[1]);
+  m.e[2][1] = cr(a[2], b[0], a[0], b[2]);
+  m.e[2][2] = cr(a[0], b[1], a[1], b[0]);
+}
+
+// Gram-Schmidt of rows 1, 2 in double, row 3 from the cross product.
+__device__ __forceinline__ void reunit_d(M3<double> &m) {
+  double n1 = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) n1 += m.e[0][k].re * m.e[0][k].re + m.e[0][k].im * m.e[0][k].im;
+  double i1 = 1.0 / sqrt(n1);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    m.e[0][k].re *= i1;
+    m.e[0][k].im *= i1;
+  }
+  double pr = 0, pi = 0;  // <r1, r2> = sum conj(r1_k) r2_k
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    pr += m.e[0][k].re * m.e[1][k].re + m.e[0][k].im * m.e[1][k].im;
+    pi += m.e[0][k].re * m.e[1][k].im - m.e[0][k].im * m.e[1][k].re;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    m.e[1][k].re -= pr * m.e[0][k].re - pi * m.e[0][k].im;
+    m.e[1][k].im -= pr * m.e[0][k].im + pi * m.e[0][k].re;
+  }
+  double n2 = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) n2 += m.e[1][k].re * m.e[1][k].re + m.e[1][k].im * m.e[1][k].im;
+  double i2 = 1.0 / sqrt(n2);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    m.e[1][k].re *= i2;
+    m.e[1][k].im *= i2;
+  }
+  third_row(m);
+}
+
+template <typename A, typename B>
+__device__ __forceinline__ M3<A> m3_cast(const M3<B> &b) {
+  M3<A> a;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) a.e[i][j] = {A(b.e[i][j].re), A(b.e[i][j].im)};
+  return a;
+}
+
+// ------------------------------------------------------------------ storage
+//
+// Links of one chain: Vec planes [layer][colour][mu][q][jj], jj the
+// checkerboard index (i_s - 1) / 2 of the site within its layer, so a warp
+// of consecutive sites reads each q-vector as one contiguous 512-byte line
+// of 128-bit loads.
+
+struct StoreF32x12 {
+  using R = float;
+  using Vec = float4;
+  static constexpr int NQ = 3;  // rows 1, 2: six complex numbers
+  __device__ static __forceinline__ M3<float> load(const Vec *plane, size_t Vh, int jj) {
+    const float4 q0 = __ldg(plane + jj), q1 = __ldg(plane + Vh + jj), q2 = __ldg(plane + 2 * Vh + jj);
+    M3<float> m;
+    m.e[0][0] = {q0.x, q0.y};
+    m.e[0][1] = {q0.z, q0.w};
+    m.e[0][2] = {q1.x, q1.y};
+    m.e[1][0] = {q1.z, q1.w};
+    m.e[1][1] = {q2.x, q2.y};
+    m.e[1][2] = {q2.z, q2.w};
+    third_row(m);
+    return m;
+  }
+  __device__ static __forceinline__ void store(Vec *plane, size_t Vh, int jj, const M3<float> &m) {
+    plane[jj] = make_float4(m.e[0][0].re, m.e[0][0].im, m.e[0][1].re, m.e[0][1].im);
+    plane[Vh + jj] = make_float4(m.e[0][2].re, m.e[0][2].im, m.e[1][0].re, m.e[1][0].im);
+    plane[2 * Vh + jj] = make_float4(m.e[1][1].re, m.e[1][1].im, m.e[1][2].re, m.e[1][2].im);
+  }
+};
+
+struct StoreF64x18 {
+  using R = double;
+  using Vec = double2;
+  static constexpr int NQ = 9;  // one complex number per 128-bit vector
+  __device__ static __forceinline__ M3<double> load(const Vec *plane, size_t Vh, int jj) {
+    M3<double> m;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const double2 v = __ldg(plane + q * Vh + jj);
+      m.e[q / 3][q % 3] = {v.x, v.y};
+    }
+    return m;
+  }
+  __device__ static __forceinline__ void store(Vec *plane, size_t Vh, int jj, const M3<double> &m) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) plane[q * Vh + jj] = make_double2(m.e[q / 3][q % 3].re, m.e[q / 3][q % 3].im);
+  }
+};
+
+template <class S>
+__device__ __forceinline__ typename S::Vec *plane_ptr(const ChainDesc &d, int layer, int colour, int mu) {
+  typename S::Vec *base = reinterpret_cast<typename S::Vec *>(d.links);
+  return base + ((size_t)((layer * 2 + colour) * d.D + mu) * S::NQ) * (size_t)d.Vh;
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC11): ten rounds; round constants
+// 0xD2511F53 / 0xCD9E8D57, key increments 0x9E3779B9 / 0xBB67AE85.
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Uniforms (w + 1/2) / 2^32 in (0,1].  In float the word is rounded to 24
+// bits first, which keeps ln(u) within ~6e-8 of the double value for every
+// u (truncating to the top 24 bits instead would quantise u near 0 and make
+// ln(u) there far less accurate).  u can round up to 1.0f, where ln(u) = 0.
+__device__ __forceinline__ float unif_f(uint32_t w) { return __fmaf_rn(__uint2float_rn(w), 0x1p-32f, 0x1p-33f); }
+__device__ __forceinline__ double unif_d(uint32_t w) { return __fma_rn((double)w, 0x1p-32, 0x1p-33); }
+
+__device__ __forceinline__ uint32_t heatbath_tag(int colour, int mu, int subgroup) {
+  return ((uint32_t)subgroup << 8) | ((uint32_t)mu << 10) | ((uint32_t)colour << 14);
+}
+
+// ------------------------------------------------------------------ SU(2) heatbath
+// Kennedy-Pendleton with the Fredenhagen-Marcu hit limit: per hit
+// X = -(ln u1 + cos^2(2 pi u2) ln u3) / alpha, accepted when
+// u4^2 <= 1 - X/2; x0 = 1 - X and (x1, x2, x3) isotropic with length
+// sqrt(X (2 - X)).  Returns false (subgroup kept) after `hits` rejections.
+
+__device__ __forceinline__ bool su2_draw_d(double alpha, int hits, uint2 key, uint32_t c0, uint32_t c1,
+                                           uint32_t tag, double x[4], uint32_t &nprop) {
+  double X = 0.0;
+  bool acc = false;
+  for (int h = 0; h < hits; ++h) {
+    const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | (uint32_t)h, kPurposeHeatbath), key);
+    ++nprop;
+    const double cs = cospi(2.0 * unif_d(w.y));
+    X = -(log(unif_d(w.x)) + cs * cs * log(unif_d(w.z))) / alpha;
+    const double u4 = unif_d(w.w);
+    if (u4 * u4 <= 1.0 - 0.5 * X) {
+      acc = true;
+      break;
+    }
+  }
+  if (!acc) return false;
+  const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | kHitDirection, kPurposeHeatbath), key);
+  const double costh = 2.0 * unif_d(w.x) - 1.0;
+  const double sinth = sqrt(1.0 - costh * costh);
+  double sphi, cphi;
+  sincospi(2.0 * unif_d(w.y), &sphi, &cphi);
+  const double rho = sqrt(X * (2.0 - X));
+  x[0] = 1.0 - X;
+  x[1] = rho * sinth * cphi;
+  x[2] = rho * sinth * sphi;
+  x[3] = rho * costh;
+  return true;
+}
+
+__device__ __forceinline__ bool su2_draw(double alpha, int hits, uint2 key, uint32_t c0, uint32_t c1, uint32_t tag,
+                                         double x[4], uint32_t &nprop) {
+  return su2_draw_d(alpha, hits, key, c0, c1, tag, x, nprop);
+}
+
+__device__ __forceinline__ bool su2_draw(float alpha, int hits, uint2 key, uint32_t c0, uint32_t c1, uint32_t tag,
+                                         float x[4], uint32_t &nprop) {
+  if (alpha >= kAlphaFp64) {
+    double xd[4];
+    const bool a = su2_draw_d((double)alpha, hits, key, c0, c1, tag, xd, nprop);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = (float)xd[i];
+    return a;
+  }
+  float X = 0.0f;
+  bool acc = false;
+  const float ia = 1.0f / alpha;
+  for (int h = 0; h < hits; ++h) {
+    const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | (uint32_t)h, kPurposeHeatbath), key);
+    ++nprop;
+    const float cs = cospif(2.0f * unif_f(w.y));
+    X = -(logf(unif_f(w.x)) + cs * cs * logf(unif_f(w.z))) * ia;
+    const float u4 = unif_f(w.w);
+    if (u4 * u4 <= 1.0f - 0.5f * X) {
+      acc = true;
+      break;
+    }
+  }
+  if (!acc) return false;
+  const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | kHitDirection, kPurposeHeatbath), key);
+  const float costh = 2.0f * unif_f(w.x) - 1.0f;
+  const float sinth = sqrtf(1.0f - costh * costh);
+  float sphi, cphi;
+  sincospif(2.0f * unif_f(w.y), &sphi, &cphi);
+  const float rho = sqrtf(X * (2.0f - X));
+  x[0] = 1.0f - X;
+  x[1] = rho * sinth * cphi;
+  x[2] = rho * sinth * sphi;
+  x[3] = rho * costh;
+  return true;
+}
+
+// ------------------------------------------------------------------ Cabibbo-Marinari
+// W = U A; for the subgroups (1,2), (1,3), (2,3): project the 2x2 block of
+// W on the quaternions a, k = |a|, alpha = 2 beta k / 3, draw x from
+// exp(alpha x0), r = x v^+ with v = a / k, and rotate rows i, j of U and W
+// by r.  Weight exp((beta/3) Re Tr(U A)).
+
+template <typename R>
+__device__ __forceinline__ void rotate_rows(M3<R> &m, int i, int j, R r0, R r1, R r2, R r3) {
+  // r = [[r0 + i r3, r2 + i r1], [-r2 + i r1, r0 - i r3]]
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const C<R> a = m.e[i][c], b = m.e[j][c];
+    m.e[i][c] = {r0 * a.re - r3 * a.im + r2 * b.re - r1 * b.im, r0 * a.im + r3 * a.re + r2 * b.im + r1 * b.re};
+    m.e[j][c] = {-r2 * a.re - r1 * a.im + r0 * b.re + r3 * b.im, -r2 * a.im + r1 * a.re + r0 * b.im - r3 * b.re};
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void cm_update(M3<R> &U, const M3<R> &A, R beta, int hits, uint2 key, uint32_t c0,
+                                          uint32_t c1, int colour, int mu, uint32_t &nprop, uint32_t &nacc) {
+  M3<R> W = mul_nn(U, A);
+#pragma unroll
+  for (int sg = 0; sg < 3; ++sg) {
+    const int i = (sg == 2) ? 1 : 0;
+    const int j = (sg == 0) ? 1 : 2;
+    const R a0 = R(0.5) * (W.e[i][i].re + W.e[j][j].re);
+    const R a1 = R(0.5) * (W.e[i][j].im + W.e[j][i].im);
+    const R a2 = R(0.5) * (W.e[i][j].re - W.e[j][i].re);
+    const R a3 = R(0.5) * (W.e[i][i].im - W.e[j][j].im);
+    const R k = sqrt(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3);
+    if (!(k > (sizeof(R) == 4 ? R(1e-30) : R(1e-300)))) continue;
+    const R alpha = R(2) * beta * k / R(3);
+    R x[4];
+    if (!su2_draw(alpha, hits, key, c0, c1, heatbath_tag(colour, mu, sg), x, nprop)) continue;
+    ++nacc;
+    const R ik = R(1) / k;
+    const R v0 = a0 * ik, v1 = a1 * ik, v2 = a2 * ik, v3 = a3 * ik;
+    // r = x v^+ as quaternions: r0 = x0 v0 + x.v, r = -x0 v + v0 x + x cross v
+    const R r0 = x[0] * v0 + x[1] * v1 + x[2] * v2 + x[3] * v3;
+    const R r1 = -x[0] * v1 + v0 * x[1] + (x[2] * v3 - x[3] * v2);
+    const R r2 = -x[0] * v2 + v0 * x[2] + (x[3] * v1 - x[1] * v3);
+    const R r3 = -x[0] * v3 + v0 * x[3] + (x[1] * v2 - x[2] * v1);
+    rotate_rows(U, i, j, r0, r1, r2, r3);
+    if (sg < 2) rotate_rows(W, i, j, r0, r1, r2, r3);
+  }
+}
+
+}  // namespace su3g

@@ -1,0 +1,83 @@
+// su3_engine.h -- data structures shared by the host runtime and the kernels.
+//
+// The engine advances a set of resident chains (lattices).  Each launch of
+// the tick kernel moves every active chain one stage forward: one
+// (colour, direction) phase of the checkerboard sweep, or a
+// re-unitarisation, or a measurement.  The stage machine lives in device
+// memory and is advanced by the last CTA of each launch, so a captured graph
+// of ticks replays without host involvement and chains of different D can
+// share a launch.
+#pragma once
+#include <cstdint>
+
+namespace su3g {
+
+constexpr int kMaxD = 4;
+
+// Stages beyond the 2D update phases.
+constexpr int kStageReunit = 100;
+constexpr int kStageMeasure = 101;
+
+// Random-number stream purposes (fourth Philox counter word).
+constexpr uint32_t kPurposeHeatbath = 0u;
+constexpr uint32_t kPurposeStart = 1u;
+constexpr uint32_t kHitDirection = 255u;
+
+// FP32 storage: an SU(2) draw with alpha at or above this value is taken in
+// double precision from the full 32-bit random words (weak-coupling links,
+// where X ~ 1/alpha is small and its relative precision sets the size of
+// the rotation).
+constexpr float kAlphaFp64 = 32.0f;
+
+// Results per measurement slot: [total, space, time, poly_re, poly_im].
+constexpr int kMeasVals = 5;
+// Partial sums per tile in a measurement: [space, time, poly_re, poly_im].
+constexpr int kPartVals = 4;
+
+struct ChainDesc {
+  void *links;               // storage base (Vec units, see su3_device.cuh)
+  double *results;           // [result_cap][nlayers + 1][kMeasVals]
+  double *partials;          // [tiles][kPartVals]
+  unsigned long long *counters;  // [proposals, accepts]
+  uint32_t seed_lo, seed_hi;
+  int32_t D, nlayers, glue_mask, layer_blind;
+  int32_t custom_period;     // 0: site key = layer*V + i_s - 1
+  int32_t dims[kMaxD];
+  int32_t period[kMaxD];
+  int32_t stride[kMaxD];     // n_a^i of eq. (i_s)
+  int32_t pstride[kMaxD];    // strides of the random-number period lattice
+  int32_t V, Vh, Vp;         // sites per layer, per colour and layer, per period lattice
+  int32_t hits;
+  int32_t reunit_every, measure_every;
+  int32_t tiles_per_layer;   // ceil(Vh / tile)
+  int32_t tile_base;         // first global tile of this chain
+  int32_t result_cap;
+  int32_t spatial_per_layer; // V / n^D (Polyakov lines per layer)
+  float beta_f;
+  double beta_d;
+};
+
+struct ChainState {
+  uint32_t sweep;          // completed sweeps (the random-number sweep counter)
+  int32_t stage;           // 0..2D-1: update phase colour*D + mu; kStageReunit; kStageMeasure
+  uint32_t target;         // the chain goes idle at the start of this sweep
+  int32_t active;          // 1: advancing; 0: idle
+  uint32_t n_meas;         // measurements recorded
+  int32_t pad[3];
+};
+
+struct EngineHeader {
+  int32_t nchains;
+  int32_t total_tiles;
+  int32_t tile;            // threads per CTA = sites per tile
+  uint32_t done_ctas;      // last-CTA detection
+};
+
+struct EngineArgs {
+  ChainDesc *desc;
+  ChainState *state;
+  EngineHeader *hdr;
+  int32_t *tile_chain;     // [total_tiles] -> chain
+};
+
+}  // namespace su3g

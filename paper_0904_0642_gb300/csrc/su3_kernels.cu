@@ -1,0 +1,543 @@
+// su3_kernels.cu -- CUDA kernels of the checkerboard SU(3) heatbath (sm_103a).
+//
+// k_tick: one persistent launch advances every resident chain by one stage
+//   (a (colour, direction) update phase, a re-unitarisation or a
+//   measurement).  One thread per site of the tile (tile = CTA width); tiles
+//   of all chains are spread over a grid of CTAs sized to the SM count.
+//   The last CTA to finish advances each chain's stage machine and reduces
+//   measurement partial sums in a fixed order.
+// k_start, k_convert, k_measure*: start configurations, canonical-layout
+//   conversion and stand-alone measurements.
+#include <cstdio>
+
+#include "su3_device.cuh"
+#include "su3_launch.h"
+
+namespace su3g {
+
+// ------------------------------------------------------------------ geometry
+
+struct SiteGeo {
+  int x[kMaxD];
+  int s;      // i_s - 1 within the layer
+  int layer;
+};
+
+// Coordinates of the site of colour `colour` at checkerboard index jj
+// (eqs. xD, x^i, i_c): the even lexicographic index 2 jj shares its row
+// with the odd one, and the colour fixes which of the two it is.
+__device__ __forceinline__ SiteGeo site_of(const ChainDesc &d, int layer, int colour, int jj) {
+  SiteGeo g;
+  int r = 2 * jj;
+  int par = colour;
+#pragma unroll
+  for (int i = 0; i < kMaxD; ++i) {
+    if (i < d.D) {
+      const int n = d.dims[i];
+      const int q = r / n;
+      g.x[i] = r - q * n;
+      r = q;
+      if (i > 0) par += g.x[i];
+    } else {
+      g.x[i] = 0;
+    }
+  }
+  par &= 1;
+  g.x[0] += par;
+  g.s = 2 * jj + par;
+  g.layer = layer;
+  return g;
+}
+
+// Lexicographic offset and layer flip of one step in direction nu.
+__device__ __forceinline__ void step_fwd(const ChainDesc &d, int xnu, int nu, int &off, int &flip) {
+  const int n = d.dims[nu], st = d.stride[nu];
+  if (xnu == n - 1) {
+    off = -(n - 1) * st;
+    flip = (d.nlayers == 2) ? ((d.glue_mask >> nu) & 1) : 0;
+  } else {
+    off = st;
+    flip = 0;
+  }
+}
+__device__ __forceinline__ void step_bwd(const ChainDesc &d, int xnu, int nu, int &off, int &flip) {
+  const int n = d.dims[nu], st = d.stride[nu];
+  if (xnu == 0) {
+    off = (n - 1) * st;
+    flip = (d.nlayers == 2) ? ((d.glue_mask >> nu) & 1) : 0;
+  } else {
+    off = -st;
+    flip = 0;
+  }
+}
+
+// Random-number site key: layer * V + i_s - 1, or the site number of
+// (x mod period) on the period lattice (identical numbers on sublattices).
+__device__ __forceinline__ uint32_t site_key(const ChainDesc &d, const SiteGeo &g) {
+  const int lay = (d.nlayers == 2 && !d.layer_blind) ? g.layer : 0;
+  if (!d.custom_period) return (uint32_t)(lay * d.V + g.s);
+  int key = 0;
+#pragma unroll
+  for (int i = 0; i < kMaxD; ++i)
+    if (i < d.D) key += (g.x[i] % d.period[i]) * d.pstride[i];
+  return (uint32_t)(lay * d.Vp + key);
+}
+
+__device__ __forceinline__ int sel(const int (&x)[kMaxD], int i) {
+  int v = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxD; ++k)
+    if (k == i) v = x[k];
+  return v;
+}
+
+// ------------------------------------------------------------------ one link update
+
+template <class S>
+__device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, int colour, int mu, int layer, int jj,
+                                            uint32_t &nprop, uint32_t &nacc) {
+  using R = typename S::R;
+  const size_t Vh = (size_t)d.Vh;
+  const SiteGeo g = site_of(d, layer, colour, jj);
+  const int oc = colour ^ 1;
+  int offp, flp;
+  step_fwd(d, sel(g.x, mu), mu, offp, flp);
+  const int sp = g.s + offp, lp = layer ^ flp;  // x + mu
+
+  M3<R> A = m3_zero<R>();
+#pragma unroll
+  for (int nu = 0; nu < kMaxD; ++nu) {
+    if (nu >= d.D || nu == mu) continue;
+    int offn, fln, offm, flm;
+    step_fwd(d, g.x[nu], nu, offn, fln);
+    step_bwd(d, g.x[nu], nu, offm, flm);
+    const int sn = g.s + offn, ln = layer ^ fln;       // x + nu
+    const int sm = g.s + offm, lm = layer ^ flm;       // x - nu
+    const int spm = sp + offm, lpm = lp ^ flm;         // x + mu - nu
+    // upper staple U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+    const M3<R> a = S::load(plane_ptr<S>(d, lp, oc, nu), Vh, sp >> 1);
+    const M3<R> b = S::load(plane_ptr<S>(d, ln, oc, mu), Vh, sn >> 1);
+    const M3<R> c = S::load(plane_ptr<S>(d, layer, colour, nu), Vh, jj);
+    const M3<R> t = mul_nd(a, b);
+    m3_acc(A, mul_nd(t, c));
+    // lower staple U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^+ U_nu(x-nu)
+    const M3<R> e = S::load(plane_ptr<S>(d, lm, oc, mu), Vh, sm >> 1);
+    const M3<R> f = S::load(plane_ptr<S>(d, lpm, colour, nu), Vh, spm >> 1);
+    const M3<R> h = S::load(plane_ptr<S>(d, lm, oc, nu), Vh, sm >> 1);
+    const M3<R> t2 = mul_nn(e, f);
+    m3_acc(A, mul_dn(t2, h));
+  }
+  typename S::Vec *pu = plane_ptr<S>(d, layer, colour, mu);
+  M3<R> U = S::load(pu, Vh, jj);
+  const R beta = sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d;
+  const uint2 key = make_uint2(d.seed_lo, d.seed_hi);
+  cm_update(U, A, beta, d.hits, key, site_key(d, g), sweep, colour, mu, nprop, nacc);
+  S::store(pu, Vh, jj, U);
+}
+
+// ------------------------------------------------------------------ re-unitarisation
+
+template <class S>
+__device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int jj) {
+  const size_t Vh = (size_t)d.Vh;
+  for (int colour = 0; colour < 2; ++colour)
+    for (int mu = 0; mu < d.D; ++mu) {
+      typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
+      M3<double> m = m3_cast<double>(S::load(p, Vh, jj));
+      reunit_d(m);
+      S::store(p, Vh, jj, m3_cast<typename S::R>(m));
+    }
+}
+
+// ------------------------------------------------------------------ measurements
+// Per thread: the two sites of checkerboard index jj (both colours).  Sums
+// in double: plaquettes split space/time, and Polyakov lines started at
+// x^D = 0 (the line follows the forward time neighbour until it closes).
+
+template <class S>
+__device__ __forceinline__ void measure_site(const ChainDesc &d, int layer, int jj, double acc[kPartVals]) {
+  using R = typename S::R;
+  const size_t Vh = (size_t)d.Vh;
+  const int D = d.D;
+  for (int colour = 0; colour < 2; ++colour) {
+    const SiteGeo g = site_of(d, layer, colour, jj);
+    const int oc = colour ^ 1;
+#pragma unroll
+    for (int mu = 0; mu < kMaxD; ++mu) {
+      if (mu >= D) continue;
+      int offp, flp;
+      step_fwd(d, g.x[mu], mu, offp, flp);
+      const M3<R> umu = S::load(plane_ptr<S>(d, layer, colour, mu), Vh, jj);
+#pragma unroll
+      for (int nu = mu + 1; nu < kMaxD; ++nu) {
+        if (nu >= D) continue;
+        int offn, fln;
+        step_fwd(d, g.x[nu], nu, offn, fln);
+        const M3<R> a = S::load(plane_ptr<S>(d, layer ^ flp, oc, nu), Vh, (g.s + offp) >> 1);  // U_nu(x+mu)
+        const M3<R> b = S::load(plane_ptr<S>(d, layer ^ fln, oc, mu), Vh, (g.s + offn) >> 1);  // U_mu(x+nu)
+        const M3<R> c = S::load(plane_ptr<S>(d, layer, colour, nu), Vh, jj);                   // U_nu(x)
+        const M3<R> P = mul_nn(umu, a);
+        const M3<R> Q = mul_nn(c, b);
+        const double p = (double)retr_nd(P, Q) * (1.0 / 3.0);
+        if (nu == D - 1) acc[1] += p; else acc[0] += p;
+      }
+    }
+    if (g.x[D - 1] == 0) {
+      // Polyakov line through (layer, x, x^D = 0)
+      const int t = D - 1;
+      M3<R> P = S::load(plane_ptr<S>(d, layer, colour, t), Vh, jj);
+      int cs = g.s, cl = layer, cc = colour, xt = 0;
+      for (int step = 0; step < 2 * d.dims[t]; ++step) {
+        int off, fl;
+        step_fwd(d, xt, t, off, fl);
+        cs += off;
+        cl ^= fl;
+        cc ^= 1;
+        xt = (xt == d.dims[t] - 1) ? 0 : xt + 1;
+        if (cs == g.s && cl == layer) break;
+        P = mul_nn(P, S::load(plane_ptr<S>(d, cl, cc, t), Vh, cs >> 1));
+      }
+      acc[2] += (double)(P.e[0][0].re + P.e[1][1].re + P.e[2][2].re) * (1.0 / 3.0);
+      acc[3] += (double)(P.e[0][0].im + P.e[1][1].im + P.e[2][2].im) * (1.0 / 3.0);
+    }
+  }
+}
+
+// Block reduction of kPartVals doubles in a fixed order (warp shuffles, then
+// warp 0 over the warp sums).  Result valid in thread 0.
+__device__ __forceinline__ void block_reduce(double v[kPartVals], double *smem /* [32][kPartVals] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < kPartVals; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < kPartVals; ++k) smem[warp * kPartVals + k] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < kPartVals; ++k) {
+      double x = lane < nw ? smem[lane * kPartVals + k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Sum the tile partials of one chain per layer (one warp, fixed order) and
+// write [total, space, time, poly_re, poly_im] for each layer and the whole.
+__device__ void finalize_measure(const ChainDesc &d, const double *partials, double *out) {
+  const int lane = threadIdx.x & 31;
+  double whole[kPartVals] = {0, 0, 0, 0};
+  const int D = d.D;
+  const double np_s = (double)d.V * (D - 1) * (D - 2) / 2, np_t = (double)d.V * (D - 1);
+  const double nl = (double)d.spatial_per_layer;
+  for (int layer = 0; layer < d.nlayers; ++layer) {
+    double v[kPartVals] = {0, 0, 0, 0};
+    for (int t = lane; t < d.tiles_per_layer; t += 32)
+#pragma unroll
+      for (int k = 0; k < kPartVals; ++k) v[k] += __ldcg(partials + (size_t)(layer * d.tiles_per_layer + t) * kPartVals + k);
+#pragma unroll
+    for (int k = 0; k < kPartVals; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+      v[k] = __shfl_sync(0xffffffffu, v[k], 0);
+      whole[k] += v[k];
+    }
+    if (lane == 0) {
+      double *o = out + layer * kMeasVals;
+      o[0] = (v[0] + v[1]) / (np_s + np_t);
+      o[1] = np_s > 0 ? v[0] / np_s : 0.0;
+      o[2] = v[1] / np_t;
+      o[3] = v[2] / nl;
+      o[4] = v[3] / nl;
+    }
+  }
+  if (lane == 0) {
+    const double L = (double)d.nlayers;
+    double *o = out + d.nlayers * kMeasVals;
+    o[0] = (whole[0] + whole[1]) / (L * (np_s + np_t));
+    o[1] = np_s > 0 ? whole[0] / (L * np_s) : 0.0;
+    o[2] = whole[1] / (L * np_t);
+    o[3] = whole[2] / (L * nl);
+    o[4] = whole[3] / (L * nl);
+  }
+}
+
+// ------------------------------------------------------------------ tick kernel
+
+__device__ __forceinline__ void load_chain(const EngineArgs &ea, int c, ChainDesc &sd, ChainState &ss) {
+  const int n1 = sizeof(ChainDesc) / 4, n2 = sizeof(ChainState) / 4;
+  const uint32_t *src1 = reinterpret_cast<const uint32_t *>(ea.desc + c);
+  const uint32_t *src2 = reinterpret_cast<const uint32_t *>(ea.state + c);
+  uint32_t *dst1 = reinterpret_cast<uint32_t *>(&sd), *dst2 = reinterpret_cast<uint32_t *>(&ss);
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) dst1[i] = src1[i];
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) dst2[i] = __ldcg(src2 + i);
+}
+
+// Next stage of a chain's stage machine (the host keeps an identical mirror):
+// the 2D update phases of a sweep, then a re-unitarisation and/or a
+// measurement when the completed-sweep count is a multiple of their
+// cadence; the chain goes idle when a sweep would start at its target.
+__device__ __host__ inline void advance_stage(const ChainDesc &d, ChainState &s) {
+  if (s.stage < 2 * d.D) {
+    s.stage += 1;
+    if (s.stage == 2 * d.D) {
+      s.sweep += 1;
+      const bool r = d.reunit_every > 0 && (s.sweep % (uint32_t)d.reunit_every) == 0;
+      const bool m = d.measure_every > 0 && (s.sweep % (uint32_t)d.measure_every) == 0;
+      s.stage = r ? kStageReunit : (m ? kStageMeasure : 0);
+    }
+  } else if (s.stage == kStageReunit) {
+    const bool m = d.measure_every > 0 && (s.sweep % (uint32_t)d.measure_every) == 0;
+    s.stage = m ? kStageMeasure : 0;
+  } else {
+    s.stage = 0;
+  }
+  if (s.stage == 0 && s.sweep >= s.target) s.active = 0;
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_tick(EngineArgs ea) {
+  __shared__ ChainDesc sd;
+  __shared__ ChainState ss;
+  __shared__ int s_chain;
+  __shared__ int s_last;
+  __shared__ double s_red[32 * kPartVals];
+  __shared__ unsigned long long s_cnt[2];
+  const int total = ea.hdr->total_tiles;
+  const int tile = blockDim.x;
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    if (threadIdx.x == 0) {
+      s_chain = ea.tile_chain[t];
+      s_cnt[0] = 0;
+      s_cnt[1] = 0;
+    }
+    __syncthreads();
+    load_chain(ea, s_chain, sd, ss);
+    __syncthreads();
+    if (ss.active) {
+      const int lt = t - sd.tile_base;
+      const int layer = lt / sd.tiles_per_layer;
+      const int jj = (lt - layer * sd.tiles_per_layer) * tile + threadIdx.x;
+      const bool valid = jj < sd.Vh;
+      if (ss.stage < 2 * sd.D) {
+        uint32_t np = 0, na = 0;
+        const int colour = ss.stage / sd.D, mu = ss.stage - colour * sd.D;
+        if (valid) update_site<S>(sd, ss.sweep, colour, mu, layer, jj, np, na);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          np += __shfl_down_sync(0xffffffffu, np, o);
+          na += __shfl_down_sync(0xffffffffu, na, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+          atomicAdd(&s_cnt[0], (unsigned long long)np);
+          atomicAdd(&s_cnt[1], (unsigned long long)na);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          atomicAdd(sd.counters + 0, s_cnt[0]);
+          atomicAdd(sd.counters + 1, s_cnt[1]);
+        }
+      } else if (ss.stage == kStageReunit) {
+        if (valid) reunit_site<S>(sd, layer, jj);
+      } else {
+        double v[kPartVals] = {0, 0, 0, 0};
+        if (valid) measure_site<S>(sd, layer, jj, v);
+        block_reduce(v, s_red);
+        if (threadIdx.x == 0)
+          for (int k = 0; k < kPartVals; ++k) sd.partials[(size_t)lt * kPartVals + k] = v[k];
+      }
+    }
+    __syncthreads();
+  }
+  // The last CTA advances the stage machines and finishes measurements.
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&ea.hdr->done_ctas, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nchains = ea.hdr->nchains;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int c = warp; c < nchains; c += nwarps) {
+    const ChainState st = ea.state[c];
+    if (st.active && st.stage == kStageMeasure) {
+      const ChainDesc &d = ea.desc[c];
+      double *out = d.results + (size_t)(st.n_meas % (uint32_t)d.result_cap) * (d.nlayers + 1) * kMeasVals;
+      finalize_measure(d, d.partials, out);
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nchains; c += blockDim.x) {
+    ChainState st = ea.state[c];
+    if (!st.active) continue;
+    if (st.stage == kStageMeasure) st.n_meas += 1;
+    advance_stage(ea.desc[c], st);
+    ea.state[c] = st;
+  }
+  if (threadIdx.x == 0) ea.hdr->done_ctas = 0;
+}
+
+// ------------------------------------------------------------------ stand-alone measurement
+
+template <class S>
+__global__ void __launch_bounds__(256) k_measure(ChainDesc *desc_dev) {
+  __shared__ double s_red[32 * kPartVals];
+  const ChainDesc d = *desc_dev;
+  const int total = d.tiles_per_layer * d.nlayers;
+  for (int lt = blockIdx.x; lt < total; lt += gridDim.x) {
+    const int layer = lt / d.tiles_per_layer;
+    const int jj = (lt - layer * d.tiles_per_layer) * blockDim.x + threadIdx.x;
+    double v[kPartVals] = {0, 0, 0, 0};
+    if (jj < d.Vh) measure_site<S>(d, layer, jj, v);
+    block_reduce(v, s_red);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < kPartVals; ++k) d.partials[(size_t)lt * kPartVals + k] = v[k];
+  }
+}
+
+__global__ void k_measure_finalize(ChainDesc *desc_dev, double *out) {
+  const ChainDesc d = *desc_dev;
+  finalize_measure(d, d.partials, out);
+}
+
+// ------------------------------------------------------------------ start configurations
+
+template <class S>
+__global__ void k_start(ChainDesc *desc_dev, int hot) {
+  const ChainDesc d = *desc_dev;
+  const size_t nl = (size_t)d.nlayers * 2 * d.D * d.Vh;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nl; i += (size_t)gridDim.x * blockDim.x) {
+    const int jj = (int)(i % d.Vh);
+    size_t r = i / d.Vh;
+    const int mu = (int)(r % d.D);
+    r /= d.D;
+    const int colour = (int)(r % 2);
+    const int layer = (int)(r / 2);
+    M3<double> m = m3_zero<double>();
+    if (!hot) {
+      m.e[0][0].re = m.e[1][1].re = m.e[2][2].re = 1.0;
+    } else {
+      // Haar SU(3): Gaussian rows 1, 2 (Box-Muller), Gram-Schmidt, cross product.
+      const SiteGeo g = site_of(d, layer, colour, jj);
+      const uint32_t key = site_key(d, g);
+      double gs[12];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const uint4 w = philox4x32_10(make_uint4(key, (uint32_t)mu, (uint32_t)b, kPurposeStart),
+                                      make_uint2(d.seed_lo, d.seed_hi));
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const double rad = sqrt(-2.0 * log(unif_d(ws[2 * p])));
+          double sn, cs;
+          sincospi(2.0 * unif_d(ws[2 * p + 1]), &sn, &cs);
+          gs[4 * b + 2 * p] = rad * cs;
+          gs[4 * b + 2 * p + 1] = rad * sn;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        m.e[0][k] = {gs[2 * k], gs[2 * k + 1]};
+        m.e[1][k] = {gs[6 + 2 * k], gs[6 + 2 * k + 1]};
+      }
+      reunit_d(m);
+    }
+    S::store(plane_ptr<S>(d, layer, colour, mu), (size_t)d.Vh, jj, m3_cast<typename S::R>(m));
+  }
+}
+
+// ------------------------------------------------------------------ canonical layout <-> storage
+
+template <class S>
+__global__ void k_convert(ChainDesc *desc_dev, double *canon, int to_canonical) {
+  const ChainDesc d = *desc_dev;
+  const size_t nlinks = (size_t)d.nlayers * d.V * d.D;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nlinks; i += (size_t)gridDim.x * blockDim.x) {
+    const int mu = (int)(i % d.D);
+    const size_t ls = i / d.D;
+    const int s = (int)(ls % d.V);
+    const int layer = (int)(ls / d.V);
+    // colour of site s: parity of its coordinate sum
+    int r = s, sum = 0;
+    for (int k = 0; k < d.D; ++k) {
+      const int n = d.dims[k];
+      sum += r % n;
+      r /= n;
+    }
+    const int colour = sum & 1;
+    typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
+    double *c = canon + i * 18;
+    if (to_canonical) {
+      const M3<typename S::R> m = S::load(p, (size_t)d.Vh, s >> 1);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          c[(a * 3 + b) * 2] = (double)m.e[a][b].re;
+          c[(a * 3 + b) * 2 + 1] = (double)m.e[a][b].im;
+        }
+    } else {
+      M3<typename S::R> m;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) m.e[a][b] = {(typename S::R)c[(a * 3 + b) * 2], (typename S::R)c[(a * 3 + b) * 2 + 1]};
+      S::store(p, (size_t)d.Vh, s >> 1, m);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <class S>
+static cudaError_t launch_tick_t(const EngineArgs &ea, int grid, int block, cudaStream_t st) {
+  k_tick<S><<<grid, block, 0, st>>>(ea);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tick(int storage, const EngineArgs &ea, int grid, int block, cudaStream_t st) {
+  return storage == 0 ? launch_tick_t<StoreF64x18>(ea, grid, block, st) : launch_tick_t<StoreF32x12>(ea, grid, block, st);
+}
+
+cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st) {
+  const int grid = tiles_total < 4096 ? tiles_total : 4096;
+  if (storage == 0)
+    k_measure<StoreF64x18><<<grid, block, 0, st>>>(desc_dev);
+  else
+    k_measure<StoreF32x12><<<grid, block, 0, st>>>(desc_dev);
+  k_measure_finalize<<<1, 32, 0, st>>>(desc_dev, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_start(int storage, ChainDesc *desc_dev, size_t nlinks, int hot, cudaStream_t st) {
+  const int block = 256;
+  const int grid = (int)((nlinks + block - 1) / block < 65536 ? (nlinks + block - 1) / block : 65536);
+  if (storage == 0)
+    k_start<StoreF64x18><<<grid, block, 0, st>>>(desc_dev, hot);
+  else
+    k_start<StoreF32x12><<<grid, block, 0, st>>>(desc_dev, hot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, double *canon, int to_canonical,
+                           cudaStream_t st) {
+  const int block = 256;
+  const int grid = (int)((nlinks + block - 1) / block < 65536 ? (nlinks + block - 1) / block : 65536);
+  if (storage == 0)
+    k_convert<StoreF64x18><<<grid, block, 0, st>>>(desc_dev, canon, to_canonical);
+  else
+    k_convert<StoreF32x12><<<grid, block, 0, st>>>(desc_dev, canon, to_canonical);
+  return cudaGetLastError();
+}
+
+cudaError_t tick_occupancy(int storage, int block, int *ctas_per_sm) {
+  if (storage == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF64x18>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF32x12>, block, 0);
+}
+
+void host_advance_stage(const ChainDesc &d, ChainState &s) { advance_stage(d, s); }
+
+}  // namespace su3g

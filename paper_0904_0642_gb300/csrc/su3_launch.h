@@ -1,0 +1,18 @@
+// su3_launch.h -- host-side entry points of the kernels in su3_kernels.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "su3_engine.h"
+
+namespace su3g {
+
+// storage: 0 = FP64 18-real, 1 = FP32 12-real.
+cudaError_t launch_tick(int storage, const EngineArgs &ea, int grid, int block, cudaStream_t st);
+cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st);
+cudaError_t launch_start(int storage, ChainDesc *desc_dev, size_t nlinks, int hot, cudaStream_t st);
+cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, double *canon, int to_canonical,
+                           cudaStream_t st);
+cudaError_t tick_occupancy(int storage, int block, int *ctas_per_sm);
+void host_advance_stage(const ChainDesc &d, ChainState &s);
+
+}  // namespace su3g

@@ -1,0 +1,82 @@
+"""The C ABI library loads and exports every symbol include/su3.h declares;
+host-side validation rejects bad arguments before any GPU work."""
+import os
+import re
+
+import pytest
+
+import paper_0904_0642_gb300 as su3
+from paper_0904_0642_gb300 import build as su3_build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "su3.h")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    su3_build.build()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(su3_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 30
+    L = su3.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(su3.EXPORTED)
+
+
+def test_version_and_defaults():
+    assert "sm_103a" in su3.su3_version()
+    c = su3.su3_config_init()
+    assert c.D == 4 and list(c.dims) == [4, 4, 4, 4] and c.beta == 6.0 and c.hits == 2
+    assert su3.su3_link_bytes(c) == 4 ** 4 * 4 * 144
+    c.storage = su3.SU3_FP32_12
+    assert su3.su3_link_bytes(c) == 4 ** 4 * 4 * 48
+    c.boundary = su3.SU3_DLT
+    assert su3.su3_link_bytes(c) == 2 * 4 ** 4 * 4 * 48
+
+
+@pytest.mark.parametrize("change,msg", [
+    (dict(dims=[4, 4, 5, 4]), "even"),
+    (dict(dims=[4, 4, 0, 4]), "even"),
+    (dict(beta=-1.0), "beta"),
+    (dict(beta=float("nan")), "beta"),
+    (dict(hits=0), "hits"),
+    (dict(storage=7), "storage"),
+    (dict(boundary=3), "boundary"),
+    (dict(rng_period=[3, 4, 4, 4]), "rng_period"),
+    (dict(glue_mask=1 << 4), "glue_mask"),
+])
+def test_invalid_configs_are_rejected(change, msg):
+    kw = dict(dims=[4, 4, 4, 4])
+    kw.update(change)
+    dims = kw.pop("dims")
+    cfg = su3.make_config(dims, **kw)
+    assert su3.su3_link_bytes(cfg) == 0
+    with pytest.raises(su3.Su3Error) as ei:
+        su3.su3_lattice_create_ex(cfg)
+    assert ei.value.status == su3.SU3_EINVAL
+    assert msg in str(ei.value)
+
+
+def test_dimension_out_of_range():
+    with pytest.raises(su3.Su3Error) as ei:
+        su3.su3_lattice_create(5, [2, 2, 2, 2, 2], su3.SU3_PBC, 6.0, 1)
+    assert ei.value.status == su3.SU3_EINVAL
+    with pytest.raises(su3.Su3Error):
+        su3.su3_lattice_create(1, [4], su3.SU3_PBC, 6.0, 1)
+
+
+def test_null_handles_are_errors():
+    L = su3.lib()
+    assert L.su3_sweep(None, 1, 1) == su3.SU3_EINVAL
+    assert L.su3_reunitarize(None) == su3.SU3_EINVAL
+    assert L.su3_ensemble_sweep(None, 1) == su3.SU3_EINVAL
+    assert L.su3_server_poll(None, 1, None) == su3.SU3_EINVAL
+    assert "NULL" in su3.su3_last_error()
