@@ -231,9 +231,9 @@ def main():
                       start=su3.SU3_START_HOT, reunit_every=SWEEPS_PER_STEP, measure_every=SWEEPS_PER_STEP,
                       measure_capacity=4096, stream=stream)
     if args.no_autotune:
-        threads, ctas, us = 128, 0, None
+        variant, threads, ctas, us = 0, 128, 0, None
     else:
-        threads, ctas, us = lat.autotune()
+        variant, threads, ctas, us = lat.autotune()
     links = lat.nlinks
     for _ in range(args.warmup):
         lat.sweep(SWEEPS_PER_STEP)
@@ -263,7 +263,8 @@ def main():
             "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "links": links,
                        "sweeps_per_step": SWEEPS_PER_STEP, "storage": "FP32 12-real", "hits": HITS, "beta": BETA,
                        "l2": "inputs larger than L2 (201 MB of links vs 129 MB L2); no flush",
-                       "launch": {"threads": threads, "ctas_per_sm": ctas, "autotune_us_per_sweep": us},
+                       "launch": {"variant": variant, "threads": threads, "ctas_per_sm": ctas,
+                                  "autotune_us_per_sweep": us},
                        "graph": True, "parallelism": f"replicas x{world}"},
             "gpu_launches": launches, "plaquette_last": plaq_last}
     clocks = clk.summary()

@@ -159,13 +159,17 @@ su3_status su3_set_sweep_counter(su3_lattice *lat, uint64_t sweeps);
 /* Number of links (D*V*layers) and device bytes of the link storage. */
 su3_status su3_lattice_info(su3_lattice *lat, size_t *links, size_t *bytes);
 
-/* Launch shape: threads per block (multiple of 32, 32..1024) and CTAs per SM
- * of the persistent update grid (0: from the occupancy calculator).  The
- * random numbers do not depend on it, so results are identical for every
- * shape.  su3_autotune times the candidates on this lattice (it advances
- * a scratch copy, not the lattice) and keeps the fastest. */
-su3_status su3_set_launch(su3_lattice *lat, int threads, int ctas_per_sm);
-su3_status su3_autotune(su3_lattice *lat, int *threads, int *ctas_per_sm, double *us_per_sweep);
+/* Launch shape.  variant: register variant of the update kernel (FP32
+ * storage: 0 = 128 registers / up to 256 threads, 1 = 96 / 128, 2 = 80 / 128;
+ * FP64 storage: 0 only).  threads: CTA width, a multiple of 32 up to the
+ * variant's maximum.  ctas_per_sm = 0 launches one CTA per tile of `threads`
+ * sites; > 0 a persistent grid of (SM count x ctas_per_sm) CTAs that loop
+ * over the tiles.  The random numbers do not depend on the shape, so results
+ * are identical for every choice.  su3_autotune times the candidates on this
+ * lattice (on a scratch copy: links, counters and sweep counter are
+ * restored) and keeps the fastest; outputs may be NULL. */
+su3_status su3_set_launch(su3_lattice *lat, int variant, int threads, int ctas_per_sm);
+su3_status su3_autotune(su3_lattice *lat, int *variant, int *threads, int *ctas_per_sm, double *us_per_sweep);
 
 /* Capture the sweep in a CUDA graph (on = 1) or launch kernel by kernel
  * (on = 0).  Results are identical either way. */
@@ -203,7 +207,11 @@ su3_status su3_ensemble_sweep(su3_ensemble *ens, int n);
  * k = total, space, time, poly_re, poly_im.  Synchronises. */
 su3_status su3_ensemble_measure(su3_ensemble *ens, double *host_out);
 su3_status su3_ensemble_get_links(su3_ensemble *ens, int chain, double *host, size_t n);
-su3_status su3_ensemble_set_launch(su3_ensemble *ens, int threads, int ctas_per_sm);
+/* As su3_measurements, for one chain of the ensemble (its measure_every). */
+su3_status su3_ensemble_measurements(su3_ensemble *ens, int chain, double *host_out, size_t max, size_t *count);
+su3_status su3_ensemble_set_launch(su3_ensemble *ens, int variant, int threads, int ctas_per_sm);
+su3_status su3_ensemble_autotune(su3_ensemble *ens, int *variant, int *threads, int *ctas_per_sm,
+                                 double *us_per_sweep);
 su3_status su3_ensemble_use_graph(su3_ensemble *ens, int on);
 /* As su3_set_profiling / su3_get_profile; stages are classified by chain 0. */
 su3_status su3_ensemble_set_profiling(su3_ensemble *ens, int on);

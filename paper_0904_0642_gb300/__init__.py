@@ -36,7 +36,7 @@ EXPORTED = [
     "su3_sweep", "su3_reunitarize", "su3_plaquette", "su3_polyakov", "su3_measure_async", "su3_measurements",
     "su3_get_links", "su3_set_links", "su3_stats", "su3_set_sweep_counter", "su3_lattice_info", "su3_set_launch",
     "su3_autotune", "su3_use_graph", "su3_set_profiling", "su3_get_profile", "su3_ensemble_create", "su3_ensemble_destroy", "su3_ensemble_sweep",
-    "su3_ensemble_measure", "su3_ensemble_get_links", "su3_ensemble_set_launch", "su3_ensemble_use_graph",
+    "su3_ensemble_measure", "su3_ensemble_get_links", "su3_ensemble_measurements", "su3_ensemble_set_launch", "su3_ensemble_autotune", "su3_ensemble_use_graph",
     "su3_ensemble_set_profiling", "su3_ensemble_get_profile",
     "su3_server_create", "su3_server_submit", "su3_server_poll", "su3_server_wait", "su3_server_load",
     "su3_server_destroy", "su3_last_error", "su3_version",
@@ -108,8 +108,8 @@ def lib():
             "su3_stats": (c_int, [vp, u64p, u64p, u64p]),
             "su3_set_sweep_counter": (c_int, [vp, c_uint64]),
             "su3_lattice_info": (c_int, [vp, POINTER(sz), POINTER(sz)]),
-            "su3_set_launch": (c_int, [vp, c_int, c_int]),
-            "su3_autotune": (c_int, [vp, POINTER(c_int), POINTER(c_int), dp]),
+            "su3_set_launch": (c_int, [vp, c_int, c_int, c_int]),
+            "su3_autotune": (c_int, [vp, POINTER(c_int), POINTER(c_int), POINTER(c_int), dp]),
             "su3_use_graph": (c_int, [vp, c_int]),
             "su3_set_profiling": (c_int, [vp, c_int]),
             "su3_get_profile": (c_int, [vp, POINTER(su3_profile), c_int]),
@@ -120,7 +120,9 @@ def lib():
             "su3_ensemble_sweep": (c_int, [vp, c_int]),
             "su3_ensemble_measure": (c_int, [vp, dp]),
             "su3_ensemble_get_links": (c_int, [vp, c_int, dp, sz]),
-            "su3_ensemble_set_launch": (c_int, [vp, c_int, c_int]),
+            "su3_ensemble_measurements": (c_int, [vp, c_int, dp, sz, POINTER(sz)]),
+            "su3_ensemble_set_launch": (c_int, [vp, c_int, c_int, c_int]),
+            "su3_ensemble_autotune": (c_int, [vp, POINTER(c_int), POINTER(c_int), POINTER(c_int), dp]),
             "su3_ensemble_use_graph": (c_int, [vp, c_int]),
             "su3_server_create": (c_int, [sz, c_int, POINTER(vp)]),
             "su3_server_submit": (c_int, [vp, POINTER(su3_job), u64p]),
@@ -244,14 +246,14 @@ def su3_lattice_info(h):
     return n.value, b.value
 
 
-def su3_set_launch(h, threads: int, ctas_per_sm: int = 0):
-    _check(lib().su3_set_launch(h, threads, ctas_per_sm))
+def su3_set_launch(h, variant: int, threads: int, ctas_per_sm: int = 0):
+    _check(lib().su3_set_launch(h, variant, threads, ctas_per_sm))
 
 
 def su3_autotune(h):
-    t, c, us = c_int(), c_int(), c_double()
-    _check(lib().su3_autotune(h, byref(t), byref(c), byref(us)))
-    return t.value, c.value, us.value
+    v, t, c, us = c_int(), c_int(), c_int(), c_double()
+    _check(lib().su3_autotune(h, byref(v), byref(t), byref(c), byref(us)))
+    return v.value, t.value, c.value, us.value
 
 
 def su3_use_graph(h, on: bool):
@@ -373,8 +375,8 @@ class Lattice:
     def set_sweep_counter(self, n):
         su3_set_sweep_counter(self.h, n)
 
-    def set_launch(self, threads, ctas_per_sm=0):
-        su3_set_launch(self.h, threads, ctas_per_sm)
+    def set_launch(self, threads, ctas_per_sm=0, variant=0):
+        su3_set_launch(self.h, variant, threads, ctas_per_sm)
 
     def autotune(self):
         return su3_autotune(self.h)
@@ -427,8 +429,21 @@ class Ensemble:
         _check(lib().su3_ensemble_get_links(self.h, chain, _dp(out), out.size))
         return out
 
-    def set_launch(self, threads, ctas_per_sm=0):
-        _check(lib().su3_ensemble_set_launch(self.h, threads, ctas_per_sm))
+    def measurements(self, chain, max_entries=1 << 16) -> np.ndarray:
+        c = self.cfgs[chain]
+        nl = 2 if c.boundary == SU3_DLT else 1
+        out = np.zeros((max_entries, 5 * (nl + 1)), dtype=np.float64)
+        cnt = c_size_t()
+        _check(lib().su3_ensemble_measurements(self.h, chain, _dp(out), max_entries, byref(cnt)))
+        return out[: cnt.value].reshape(cnt.value, nl + 1, 5)
+
+    def set_launch(self, threads, ctas_per_sm=0, variant=0):
+        _check(lib().su3_ensemble_set_launch(self.h, variant, threads, ctas_per_sm))
+
+    def autotune(self):
+        v, t, c, us = c_int(), c_int(), c_int(), c_double()
+        _check(lib().su3_ensemble_autotune(self.h, byref(v), byref(t), byref(c), byref(us)))
+        return v.value, t.value, c.value, us.value
 
     def use_graph(self, on=True):
         _check(lib().su3_ensemble_use_graph(self.h, int(bool(on))))

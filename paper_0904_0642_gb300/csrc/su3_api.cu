@@ -84,7 +84,8 @@ static su3_status validate(const su3_config *c) {
   }
   const int layers = c->boundary == SU3_DLT ? 2 : 1;
   if (c->boundary != SU3_PBC && c->boundary != SU3_DLT) return fail(SU3_EINVAL, "unknown boundary %d", c->boundary);
-  if (V * layers * 4 > 0x7fffffffLL) return fail(SU3_EINVAL, "lattice too large for 32-bit site keys");
+  if (V * layers * c->D * 9 >= 0x7fffffffLL)
+    return fail(SU3_EINVAL, "lattice too large: link storage must stay below 2^31 16-byte vectors");
   if (!(c->beta >= 0.0) || !std::isfinite(c->beta)) return fail(SU3_EINVAL, "beta=%g must be finite and >= 0", c->beta);
   if (c->hits < 1 || c->hits > 254) return fail(SU3_EINVAL, "hits=%d outside 1..254", c->hits);
   if (c->storage != SU3_FP64_18 && c->storage != SU3_FP32_12) return fail(SU3_EINVAL, "unknown storage %d", c->storage);
@@ -179,6 +180,14 @@ static void fill_desc(Chain &ch, int tile) {
   d.tiles_per_layer = (d.Vh + tile - 1) / tile;
   d.result_cap = c.measure_capacity > 0 ? c.measure_capacity : 1024;
   d.spatial_per_layer = V / c.dims[c.D - 1];
+  d.pow2 = 1;
+  for (int i = 0; i < kMaxD; ++i) {
+    d.shift[i] = 0;
+    if (i < c.D) {
+      if (c.dims[i] & (c.dims[i] - 1)) d.pow2 = 0;
+      while ((1 << d.shift[i]) < c.dims[i]) ++d.shift[i];
+    }
+  }
   d.beta_f = (float)c.beta;
   d.beta_d = c.beta;
 }
@@ -197,6 +206,7 @@ struct Engine {
   double *h_pinned = nullptr;    // small pinned staging (results, counters)
   int block = 128;
   int ctas_per_sm = 0;
+  int variant = 0;  // register variant of the tick kernel (launch_tick)
   int total_tiles = 0;
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
@@ -235,7 +245,7 @@ struct Engine {
       CU(cudaEventCreate(&p.a));
       CU(cudaEventCreate(&p.b));
       CU(cudaEventRecord(p.a, stream));
-      CU(launch_tick(storage, args(), grid, block, stream));
+      CU(launch_tick(storage, variant, args(), grid, block, stream));
       CU(cudaEventRecord(p.b, stream));
       prof_pending.push_back(p);
       if (s.active) {
@@ -368,6 +378,7 @@ struct Engine {
 
   // Rebuild tile bases and the tile -> chain map; upload descriptors.
   su3_status rebuild() {
+    const int old_tiles = total_tiles;
     int tiles = 0;
     for (auto &ch : chains) {
       fill_desc(ch, block);
@@ -375,6 +386,7 @@ struct Engine {
       tiles += ch.desc.nlayers * ch.desc.tiles_per_layer;
     }
     total_tiles = tiles;
+    if (ctas_per_sm <= 0 && tiles != old_tiles) drop_graph();  // the grid follows the tile count
     if (chains.size() > chain_cap) {
       cudaFree(d_desc);
       cudaFree(d_state);
@@ -402,7 +414,7 @@ struct Engine {
     h.nchains = (int32_t)chains.size();
     h.total_tiles = tiles;
     h.tile = block;
-    h.done_ctas = 0;
+    h.done_warps = 0;
     // Pageable copies are staged by the driver before the call returns.
     if (tiles) CU(cudaMemcpyAsync(d_tile_chain, map.data(), tiles * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
     if (!chains.empty()) {
@@ -445,15 +457,16 @@ struct Engine {
     graph_ticks = 0;
   }
 
+  // ctas_per_sm = 0: one CTA per tile (the hardware balances the tail);
+  // > 0: a persistent grid of SMs x ctas_per_sm CTAs looping over tiles.
   su3_status grid_size(int *grid) {
+    if (ctas_per_sm <= 0) {
+      *grid = std::max(1, total_tiles);
+      return SU3_OK;
+    }
     int nsm = 0;
     TRY(device_sm_count(&nsm));
-    int occ = ctas_per_sm;
-    if (occ <= 0) {
-      CU(tick_occupancy(storage, block, &occ));
-      if (occ < 1) occ = 1;
-    }
-    *grid = std::max(1, std::min(total_tiles, nsm * occ));
+    *grid = std::max(1, std::min(total_tiles, nsm * ctas_per_sm));
     return SU3_OK;
   }
 
@@ -462,7 +475,7 @@ struct Engine {
   su3_status tick_direct(int n) {
     int grid = 0;
     TRY(grid_size(&grid));
-    for (int i = 0; i < n; ++i) CU(launch_tick(storage, args(), grid, block, stream));
+    for (int i = 0; i < n; ++i) CU(launch_tick(storage, variant, args(), grid, block, stream));
     return SU3_OK;
   }
 
@@ -475,7 +488,7 @@ struct Engine {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kGraphTicks; ++i) {
-      cudaError_t e = launch_tick(storage, args(), grid, block, stream);
+      cudaError_t e = launch_tick(storage, variant, args(), grid, block, stream);
       if (e != cudaSuccess) {
         cudaStreamEndCapture(stream, &g);
         if (g) cudaGraphDestroy(g);
@@ -595,11 +608,15 @@ struct Engine {
     return SU3_OK;
   }
 
-  su3_status set_launch(int threads, int ctas) {
-    if (threads < 32 || threads > 256 || (threads & 31))
-      return fail(SU3_EINVAL, "threads=%d must be a multiple of 32 in 32..256", threads);
+  su3_status set_launch(int var, int threads, int ctas) {
+    if (var < 0 || var >= tick_variants(storage))
+      return fail(SU3_EINVAL, "variant=%d outside 0..%d", var, tick_variants(storage) - 1);
+    const int tmax = tick_max_threads(storage, var);
+    if (threads < 32 || threads > tmax || (threads & 31))
+      return fail(SU3_EINVAL, "threads=%d must be a multiple of 32 in 32..%d", threads, tmax);
     if (ctas < 0 || ctas > 64) return fail(SU3_EINVAL, "ctas_per_sm=%d outside 0..64", ctas);
     CU(cudaStreamSynchronize(stream));
+    variant = var;
     block = threads;
     ctas_per_sm = ctas;
     drop_graph();
@@ -725,10 +742,9 @@ extern "C" su3_status su3_measure_async(su3_lattice *lat, double *device_out) {
   return SU3_OK;
 }
 
-extern "C" su3_status su3_measurements(su3_lattice *lat, double *host_out, size_t max, size_t *count) {
-  LAT_CHECK(lat);
-  Engine &e = lat->eng;
-  Chain &ch = e.chains[0];
+static su3_status chain_measurements(Engine &e, size_t c, double *host_out, size_t max, size_t *count) {
+  if (!host_out && max) return fail(SU3_EINVAL, "host_out is NULL");
+  Chain &ch = e.chains[c];
   const size_t per = (size_t)(ch.desc.nlayers + 1) * kMeasVals;
   const uint32_t n = ch.state.n_meas;
   const size_t cap = (size_t)ch.desc.result_cap;
@@ -744,6 +760,11 @@ extern "C" su3_status su3_measurements(su3_lattice *lat, double *host_out, size_
   }
   if (count) *count = take;
   return SU3_OK;
+}
+
+extern "C" su3_status su3_measurements(su3_lattice *lat, double *host_out, size_t max, size_t *count) {
+  LAT_CHECK(lat);
+  return chain_measurements(lat->eng, 0, host_out, max, count);
 }
 
 extern "C" su3_status su3_get_links(su3_lattice *lat, double *host, size_t n) {
@@ -781,9 +802,9 @@ extern "C" su3_status su3_lattice_info(su3_lattice *lat, size_t *links, size_t *
   return SU3_OK;
 }
 
-extern "C" su3_status su3_set_launch(su3_lattice *lat, int threads, int ctas_per_sm) {
+extern "C" su3_status su3_set_launch(su3_lattice *lat, int variant, int threads, int ctas_per_sm) {
   LAT_CHECK(lat);
-  return lat->eng.set_launch(threads, ctas_per_sm);
+  return lat->eng.set_launch(variant, threads, ctas_per_sm);
 }
 
 extern "C" su3_status su3_use_graph(su3_lattice *lat, int on) {
@@ -807,7 +828,7 @@ extern "C" su3_status su3_get_profile(su3_lattice *lat, su3_profile *out, int re
 
 // Time candidate launch shapes on a scratch copy of the links (the lattice,
 // its counters and its stage machine are restored afterwards).
-static su3_status autotune_engine(Engine &e, int *threads, int *ctas, double *us) {
+static su3_status autotune_engine(Engine &e, int *variant, int *threads, int *ctas, double *us) {
   if (e.tiles_dirty) TRY(e.rebuild());
   CU(cudaStreamSynchronize(e.stream));
   std::vector<void *> backup(e.chains.size(), nullptr);
@@ -822,7 +843,7 @@ static su3_status autotune_engine(Engine &e, int *threads, int *ctas, double *us
     CU(cudaMemcpyAsync(&saved_cnt[2 * c], e.chains[c].counters, 16, cudaMemcpyDeviceToHost, e.stream));
   }
   CU(cudaStreamSynchronize(e.stream));
-  const int saved_block = e.block, saved_ctas = e.ctas_per_sm;
+  const int saved_var = e.variant, saved_block = e.block, saved_ctas = e.ctas_per_sm;
   const bool saved_graph = e.use_graph, saved_prof = e.profiling;
   e.profiling = false;
   std::vector<int> saved_meas;
@@ -834,31 +855,35 @@ static su3_status autotune_engine(Engine &e, int *threads, int *ctas, double *us
   CU(cudaEventCreate(&a));
   CU(cudaEventCreate(&b));
   double best = 1e30;
-  int best_t = saved_block, best_c = saved_ctas;
+  int best_v = saved_var, best_t = saved_block, best_c = saved_ctas;
   const int cand_t[] = {64, 128, 256};
   su3_status st = SU3_OK;
-  for (int t : cand_t) {
-    int occ = 0;
-    if (tick_occupancy(e.storage, t, &occ) != cudaSuccess || occ < 1) continue;
-    for (int c = 1; c <= occ && st == SU3_OK; c = (c < occ && 2 * c > occ) ? occ : 2 * c) {
-      if ((st = e.set_launch(t, c)) != SU3_OK) break;
-      e.use_graph = true;
-      if ((st = e.sweep_all(1)) != SU3_OK) break;  // warm-up + graph capture
-      cudaEventRecord(a, e.stream);
-      const int reps = 3;
-      if ((st = e.sweep_all(reps)) != SU3_OK) break;
-      cudaEventRecord(b, e.stream);
-      cudaEventSynchronize(b);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, a, b);
-      const double per = 1e3 * ms / reps;
-      if (per < best) {
-        best = per;
-        best_t = t;
-        best_c = c;
+  for (int v = 0; v < tick_variants(e.storage) && st == SU3_OK; ++v)
+    for (int t : cand_t) {
+      if (t > tick_max_threads(e.storage, v)) continue;
+      int occ = 0;
+      if (tick_occupancy(e.storage, v, t, &occ) != cudaSuccess || occ < 1) continue;
+      // 0 = one CTA per tile, then persistent grids of 1, 2, 4, ..., occ CTAs per SM
+      for (int c = 0; c <= occ && st == SU3_OK; c = (c == 0) ? 1 : ((c < occ && 2 * c > occ) ? occ : 2 * c)) {
+        if ((st = e.set_launch(v, t, c)) != SU3_OK) break;
+        e.use_graph = true;
+        if ((st = e.sweep_all(1)) != SU3_OK) break;  // warm-up + graph capture
+        cudaEventRecord(a, e.stream);
+        const int reps = 3;
+        if ((st = e.sweep_all(reps)) != SU3_OK) break;
+        cudaEventRecord(b, e.stream);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        const double per = 1e3 * ms / reps;
+        if (per < best) {
+          best = per;
+          best_v = v;
+          best_t = t;
+          best_c = c;
+        }
       }
     }
-  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   for (size_t c = 0; c < e.chains.size(); ++c) {
@@ -872,17 +897,19 @@ static su3_status autotune_engine(Engine &e, int *threads, int *ctas, double *us
   e.profiling = saved_prof;
   if (st != SU3_OK) return st;
   e.use_graph = saved_graph;
-  TRY(e.set_launch(best_t, best_c));
+  TRY(e.set_launch(best_v, best_t, best_c));
   TRY(e.rebuild());
+  if (variant) *variant = best_v;
   if (threads) *threads = best_t;
   if (ctas) *ctas = best_c;
   if (us) *us = best;
   return SU3_OK;
 }
 
-extern "C" su3_status su3_autotune(su3_lattice *lat, int *threads, int *ctas_per_sm, double *us_per_sweep) {
+extern "C" su3_status su3_autotune(su3_lattice *lat, int *variant, int *threads, int *ctas_per_sm,
+                                   double *us_per_sweep) {
   LAT_CHECK(lat);
-  return autotune_engine(lat->eng, threads, ctas_per_sm, us_per_sweep);
+  return autotune_engine(lat->eng, variant, threads, ctas_per_sm, us_per_sweep);
 }
 
 // ------------------------------------------------------------------ ensembles
@@ -946,9 +973,22 @@ extern "C" su3_status su3_ensemble_get_links(su3_ensemble *ens, int chain, doubl
   return ens->eng.get_links((size_t)chain, host, n);
 }
 
-extern "C" su3_status su3_ensemble_set_launch(su3_ensemble *ens, int threads, int ctas_per_sm) {
+extern "C" su3_status su3_ensemble_measurements(su3_ensemble *ens, int chain, double *host_out, size_t max,
+                                                size_t *count) {
   if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
-  return ens->eng.set_launch(threads, ctas_per_sm);
+  if (chain < 0 || (size_t)chain >= ens->eng.chains.size()) return fail(SU3_EINVAL, "chain %d out of range", chain);
+  return chain_measurements(ens->eng, (size_t)chain, host_out, max, count);
+}
+
+extern "C" su3_status su3_ensemble_set_launch(su3_ensemble *ens, int variant, int threads, int ctas_per_sm) {
+  if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
+  return ens->eng.set_launch(variant, threads, ctas_per_sm);
+}
+
+extern "C" su3_status su3_ensemble_autotune(su3_ensemble *ens, int *variant, int *threads, int *ctas_per_sm,
+                                            double *us_per_sweep) {
+  if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
+  return autotune_engine(ens->eng, variant, threads, ctas_per_sm, us_per_sweep);
 }
 
 extern "C" su3_status su3_ensemble_use_graph(su3_ensemble *ens, int on) {
@@ -1034,6 +1074,13 @@ extern "C" su3_status su3_server_create(size_t hbm_budget_bytes, int max_slots, 
   }
   srv->budget = hbm_budget_bytes;
   srv->max_slots = max_slots;
+  {
+    // persistent grid: its size does not depend on the resident jobs, so the
+    // captured graph of ticks survives admissions and retirements
+    int occ = 0;
+    if (tick_occupancy(SU3_FP32_12, srv->eng.variant, srv->eng.block, &occ) != cudaSuccess || occ < 1) occ = 1;
+    srv->eng.ctas_per_sm = occ;
+  }
   srv->t0 = std::chrono::steady_clock::now();
   srv->worker = std::thread([srv] { srv->loop(); });
   *out = srv;

@@ -31,65 +31,105 @@ __device__ __forceinline__ M3<R> m3_zero() {
   return m;
 }
 
-// c = a b
+// Fused multiply-add in the working precision.  The complex algebra below
+// is written as explicit FMA chains: `s += a*b - c*d` would otherwise be
+// compiled as FMUL + FFMA + FADD (C semantics forbid the reassociation).
+__device__ __forceinline__ float fm(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fm(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// s += a b
 template <typename R>
+__device__ __forceinline__ void cmac(C<R> &s, const C<R> &a, const C<R> &b) {
+  s.re = fm(a.re, b.re, s.re);
+  s.re = fm(-a.im, b.im, s.re);
+  s.im = fm(a.re, b.im, s.im);
+  s.im = fm(a.im, b.re, s.im);
+}
+// s += a conj(b)
+template <typename R>
+__device__ __forceinline__ void cmac_nc(C<R> &s, const C<R> &a, const C<R> &b) {
+  s.re = fm(a.re, b.re, s.re);
+  s.re = fm(a.im, b.im, s.re);
+  s.im = fm(a.im, b.re, s.im);
+  s.im = fm(-a.re, b.im, s.im);
+}
+// s += conj(a) b
+template <typename R>
+__device__ __forceinline__ void cmac_cn(C<R> &s, const C<R> &a, const C<R> &b) {
+  s.re = fm(a.re, b.re, s.re);
+  s.re = fm(a.im, b.im, s.re);
+  s.im = fm(a.re, b.im, s.im);
+  s.im = fm(-a.im, b.re, s.im);
+}
+template <typename R>
+__device__ __forceinline__ C<R> cmul(const C<R> &a, const C<R> &b) {
+  return {fm(-a.im, b.im, a.re * b.re), fm(a.im, b.re, a.re * b.im)};
+}
+template <typename R>
+__device__ __forceinline__ C<R> cmul_nc(const C<R> &a, const C<R> &b) {
+  return {fm(a.im, b.im, a.re * b.re), fm(-a.re, b.im, a.im * b.re)};
+}
+template <typename R>
+__device__ __forceinline__ C<R> cmul_cn(const C<R> &a, const C<R> &b) {
+  return {fm(a.im, b.im, a.re * b.re), fm(-a.im, b.re, a.re * b.im)};
+}
+
+// c = a b (rows 0..NR-1)
+template <int NR = 3, typename R>
 __device__ __forceinline__ M3<R> mul_nn(const M3<R> &a, const M3<R> &b) {
   M3<R> c;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < NR; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      R re = a.e[i][0].re * b.e[0][j].re - a.e[i][0].im * b.e[0][j].im;
-      R im = a.e[i][0].re * b.e[0][j].im + a.e[i][0].im * b.e[0][j].re;
-#pragma unroll
-      for (int k = 1; k < 3; ++k) {
-        re += a.e[i][k].re * b.e[k][j].re - a.e[i][k].im * b.e[k][j].im;
-        im += a.e[i][k].re * b.e[k][j].im + a.e[i][k].im * b.e[k][j].re;
-      }
-      c.e[i][j] = {re, im};
+      C<R> s = cmul(a.e[i][0], b.e[0][j]);
+      cmac(s, a.e[i][1], b.e[1][j]);
+      cmac(s, a.e[i][2], b.e[2][j]);
+      c.e[i][j] = s;
     }
   return c;
 }
 
-// c = a b^+
-template <typename R>
+// c = a b^+ (rows 0..NR-1)
+template <int NR = 3, typename R>
 __device__ __forceinline__ M3<R> mul_nd(const M3<R> &a, const M3<R> &b) {
   M3<R> c;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < NR; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      R re = a.e[i][0].re * b.e[j][0].re + a.e[i][0].im * b.e[j][0].im;
-      R im = a.e[i][0].im * b.e[j][0].re - a.e[i][0].re * b.e[j][0].im;
-#pragma unroll
-      for (int k = 1; k < 3; ++k) {
-        re += a.e[i][k].re * b.e[j][k].re + a.e[i][k].im * b.e[j][k].im;
-        im += a.e[i][k].im * b.e[j][k].re - a.e[i][k].re * b.e[j][k].im;
-      }
-      c.e[i][j] = {re, im};
+      C<R> s = cmul_nc(a.e[i][0], b.e[j][0]);
+      cmac_nc(s, a.e[i][1], b.e[j][1]);
+      cmac_nc(s, a.e[i][2], b.e[j][2]);
+      c.e[i][j] = s;
     }
   return c;
 }
 
-// c = a^+ b
-template <typename R>
+// c = a^+ b (rows 0..NR-1)
+template <int NR = 3, typename R>
 __device__ __forceinline__ M3<R> mul_dn(const M3<R> &a, const M3<R> &b) {
   M3<R> c;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < NR; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      R re = a.e[0][i].re * b.e[0][j].re + a.e[0][i].im * b.e[0][j].im;
-      R im = a.e[0][i].re * b.e[0][j].im - a.e[0][i].im * b.e[0][j].re;
-#pragma unroll
-      for (int k = 1; k < 3; ++k) {
-        re += a.e[k][i].re * b.e[k][j].re + a.e[k][i].im * b.e[k][j].im;
-        im += a.e[k][i].re * b.e[k][j].im - a.e[k][i].im * b.e[k][j].re;
-      }
-      c.e[i][j] = {re, im};
+      C<R> s = cmul_cn(a.e[0][i], b.e[0][j]);
+      cmac_cn(s, a.e[1][i], b.e[1][j]);
+      cmac_cn(s, a.e[2][i], b.e[2][j]);
+      c.e[i][j] = s;
     }
   return c;
 }
+
+// Two-row forms: a product of SU(3) factors is SU(3), so only rows 0, 1 are
+// computed and row 2 is completed by third_row (24 FMA instead of 36).
+template <typename R>
+__device__ __forceinline__ M3<R> mul_nn_2(const M3<R> &a, const M3<R> &b) { return mul_nn<2>(a, b); }
+template <typename R>
+__device__ __forceinline__ M3<R> mul_nd_2(const M3<R> &a, const M3<R> &b) { return mul_nd<2>(a, b); }
+template <typename R>
+__device__ __forceinline__ M3<R> mul_dn_2(const M3<R> &a, const M3<R> &b) { return mul_dn<2>(a, b); }
 
 template <typename R>
 __device__ __forceinline__ void m3_acc(M3<R> &a, const M3<R> &b) {
@@ -105,27 +145,79 @@ __device__ __forceinline__ void m3_acc(M3<R> &a, const M3<R> &b) {
 // Re Tr(a b^+) = sum_ij Re(a_ij conj(b_ij))
 template <typename R>
 __device__ __forceinline__ R retr_nd(const M3<R> &a, const M3<R> &b) {
-  R s = R(0);
+  R s = a.e[0][0].re * b.e[0][0].re;
+  s = fm(a.e[0][0].im, b.e[0][0].im, s);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) s += a.e[i][j].re * b.e[i][j].re + a.e[i][j].im * b.e[i][j].im;
+    for (int j = 0; j < 3; ++j) {
+      if (i == 0 && j == 0) continue;
+      s = fm(a.e[i][j].re, b.e[i][j].re, s);
+      s = fm(a.e[i][j].im, b.e[i][j].im, s);
+    }
   return s;
+}
+
+// conj(p q - r s)
+template <typename R>
+__device__ __forceinline__ C<R> conj_cross(const C<R> &p, const C<R> &q, const C<R> &r, const C<R> &s) {
+  R re = p.re * q.re;
+  re = fm(-p.im, q.im, re);
+  re = fm(-r.re, s.re, re);
+  re = fm(r.im, s.im, re);
+  R im = -(p.re * q.im);
+  im = fm(-p.im, q.re, im);
+  im = fm(r.re, s.im, im);
+  im = fm(r.im, s.re, im);
+  return {re, im};
 }
 
 // Third row of an SU(3) matrix from the first two: conj(row1 x row2).
 template <typename R>
 __device__ __forceinline__ void third_row(M3<R> &m) {
   const C<R> *a = m.e[0], *b = m.e[1];
-  // (p q - r s)^* for the cross product components
-  auto cr = [](C<R> p, C<R> q, C<R> r, C<R> s) -> C<R> {
-    R re = p.re * q.re - p.im * q.im - (r.re * s.re - r.im * s.im);
-    R im = p.re * q.im + p.im * q.re - (r.re * s.im + r.im * s.re);
-    return {re, -im};
-  };
-  m.e[2][0] = cr(a[1], b[2], a[2], b[1]);
-  m.e[2][1] = cr(a[2], b[0], a[0], b[2]);
-  m.e[2][2] = cr(a[0], b[1], a[1], b[0]);
+  m.e[2][0] = conj_cross(a[1], b[2], a[2], b[1]);
+  m.e[2][1] = conj_cross(a[2], b[0], a[0], b[2]);
+  m.e[2][2] = conj_cross(a[0], b[1], a[1], b[0]);
+}
+
+// A += m for an SU(3) matrix m given by rows 0, 1: row 2 of m is
+// accumulated straight from the cross product.
+template <typename R>
+__device__ __forceinline__ void acc_su3_2rows(M3<R> &A, const M3<R> &m) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      A.e[i][j].re += m.e[i][j].re;
+      A.e[i][j].im += m.e[i][j].im;
+    }
+  const C<R> *a = m.e[0], *b = m.e[1];
+  const int P[3][4] = {{1, 2, 2, 1}, {2, 0, 0, 2}, {0, 1, 1, 0}};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const C<R> &p = a[P[j][0]], &q = b[P[j][1]], &r = a[P[j][2]], &t = b[P[j][3]];
+    // A_2j += conj(p q - r t)
+    R re = fm(p.re, q.re, A.e[2][j].re);
+    re = fm(-p.im, q.im, re);
+    re = fm(-r.re, t.re, re);
+    re = fm(r.im, t.im, re);
+    R im = fm(-p.re, q.im, A.e[2][j].im);
+    im = fm(-p.im, q.re, im);
+    im = fm(r.re, t.im, im);
+    im = fm(r.im, t.re, im);
+    A.e[2][j] = {re, im};
+  }
+}
+
+// 1/sqrt(n) in double: a float seed refined by two Newton steps,
+// y <- y (3 - n y^2) / 2; each roughly squares the relative error
+// (~2e-7 -> ~1e-13 -> rounding level).
+__device__ __forceinline__ double rsqrt_d(double n) {
+  double y = (double)rsqrtf((float)n);
+  const double h = 0.5 * n;
+  y = y * __fma_rn(-h * y, y, 1.5);
+  return y * __fma_rn(-h * y, y, 1.5);
 }
 
 // Gram-Schmidt of rows 1, 2 in double, row 3 from the cross product.
@@ -133,7 +225,7 @@ __device__ __forceinline__ void reunit_d(M3<double> &m) {
   double n1 = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) n1 += m.e[0][k].re * m.e[0][k].re + m.e[0][k].im * m.e[0][k].im;
-  double i1 = 1.0 / sqrt(n1);
+  double i1 = rsqrt_d(n1);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     m.e[0][k].re *= i1;
@@ -153,7 +245,7 @@ __device__ __forceinline__ void reunit_d(M3<double> &m) {
   double n2 = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) n2 += m.e[1][k].re * m.e[1][k].re + m.e[1][k].im * m.e[1][k].im;
-  double i2 = 1.0 / sqrt(n2);
+  double i2 = rsqrt_d(n2);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     m.e[1][k].re *= i2;
@@ -183,8 +275,10 @@ struct StoreF32x12 {
   using R = float;
   using Vec = float4;
   static constexpr int NQ = 3;  // rows 1, 2: six complex numbers
-  __device__ static __forceinline__ M3<float> load(const Vec *plane, size_t Vh, int jj) {
-    const float4 q0 = __ldg(plane + jj), q1 = __ldg(plane + Vh + jj), q2 = __ldg(plane + 2 * Vh + jj);
+  // rows 0, 1 only (row 2 left unset)
+  __device__ static __forceinline__ M3<float> load2(const Vec *plane, int Vh, int jj) {
+    const Vec *p = plane + jj;
+    const float4 q0 = __ldg(p), q1 = __ldg(p + Vh), q2 = __ldg(p + 2 * Vh);
     M3<float> m;
     m.e[0][0] = {q0.x, q0.y};
     m.e[0][1] = {q0.z, q0.w};
@@ -192,13 +286,18 @@ struct StoreF32x12 {
     m.e[1][0] = {q1.z, q1.w};
     m.e[1][1] = {q2.x, q2.y};
     m.e[1][2] = {q2.z, q2.w};
+    return m;
+  }
+  __device__ static __forceinline__ M3<float> load(const Vec *plane, int Vh, int jj) {
+    M3<float> m = load2(plane, Vh, jj);
     third_row(m);
     return m;
   }
-  __device__ static __forceinline__ void store(Vec *plane, size_t Vh, int jj, const M3<float> &m) {
-    plane[jj] = make_float4(m.e[0][0].re, m.e[0][0].im, m.e[0][1].re, m.e[0][1].im);
-    plane[Vh + jj] = make_float4(m.e[0][2].re, m.e[0][2].im, m.e[1][0].re, m.e[1][0].im);
-    plane[2 * Vh + jj] = make_float4(m.e[1][1].re, m.e[1][1].im, m.e[1][2].re, m.e[1][2].im);
+  __device__ static __forceinline__ void store(Vec *plane, int Vh, int jj, const M3<float> &m) {
+    Vec *p = plane + jj;
+    p[0] = make_float4(m.e[0][0].re, m.e[0][0].im, m.e[0][1].re, m.e[0][1].im);
+    p[Vh] = make_float4(m.e[0][2].re, m.e[0][2].im, m.e[1][0].re, m.e[1][0].im);
+    p[2 * Vh] = make_float4(m.e[1][1].re, m.e[1][1].im, m.e[1][2].re, m.e[1][2].im);
   }
 };
 
@@ -206,25 +305,39 @@ struct StoreF64x18 {
   using R = double;
   using Vec = double2;
   static constexpr int NQ = 9;  // one complex number per 128-bit vector
-  __device__ static __forceinline__ M3<double> load(const Vec *plane, size_t Vh, int jj) {
+  __device__ static __forceinline__ M3<double> load(const Vec *plane, int Vh, int jj) {
+    const Vec *p = plane + jj;
     M3<double> m;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-      const double2 v = __ldg(plane + q * Vh + jj);
+      const double2 v = __ldg(p + q * Vh);
       m.e[q / 3][q % 3] = {v.x, v.y};
     }
     return m;
   }
-  __device__ static __forceinline__ void store(Vec *plane, size_t Vh, int jj, const M3<double> &m) {
+  __device__ static __forceinline__ M3<double> load2(const Vec *plane, int Vh, int jj) {
+    const Vec *p = plane + jj;
+    M3<double> m;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) plane[q * Vh + jj] = make_double2(m.e[q / 3][q % 3].re, m.e[q / 3][q % 3].im);
+    for (int q = 0; q < 6; ++q) {
+      const double2 v = __ldg(p + q * Vh);
+      m.e[q / 3][q % 3] = {v.x, v.y};
+    }
+    return m;
+  }
+  __device__ static __forceinline__ void store(Vec *plane, int Vh, int jj, const M3<double> &m) {
+    Vec *p = plane + jj;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) p[q * Vh] = make_double2(m.e[q / 3][q % 3].re, m.e[q / 3][q % 3].im);
   }
 };
 
+// The (layer, colour, mu) plane of a chain's links.  Offsets stay in 32 bits
+// (the host rejects chains with 2^31 vectors or more).
 template <class S>
 __device__ __forceinline__ typename S::Vec *plane_ptr(const ChainDesc &d, int layer, int colour, int mu) {
   typename S::Vec *base = reinterpret_cast<typename S::Vec *>(d.links);
-  return base + ((size_t)((layer * 2 + colour) * d.D + mu) * S::NQ) * (size_t)d.Vh;
+  return base + ((layer * 2 + colour) * d.D + mu) * (S::NQ * d.Vh);
 }
 
 // ------------------------------------------------------------------ Philox4x32-10

@@ -53,6 +53,8 @@ struct ChainDesc {
   int32_t tile_base;         // first global tile of this chain
   int32_t result_cap;
   int32_t spatial_per_layer; // V / n^D (Polyakov lines per layer)
+  int32_t pow2;              // 1: every extent is a power of two (coordinates by shifts)
+  int32_t shift[kMaxD];      // log2 n^i when pow2
   float beta_f;
   double beta_d;
 };
@@ -70,7 +72,7 @@ struct EngineHeader {
   int32_t nchains;
   int32_t total_tiles;
   int32_t tile;            // threads per CTA = sites per tile
-  uint32_t done_ctas;      // last-CTA detection
+  uint32_t done_warps;     // last-warp detection (the last warp to finish runs the stage machines)
 };
 
 struct EngineArgs {

@@ -30,16 +30,29 @@ __device__ __forceinline__ SiteGeo site_of(const ChainDesc &d, int layer, int co
   SiteGeo g;
   int r = 2 * jj;
   int par = colour;
+  if (d.pow2) {
 #pragma unroll
-  for (int i = 0; i < kMaxD; ++i) {
-    if (i < d.D) {
-      const int n = d.dims[i];
-      const int q = r / n;
-      g.x[i] = r - q * n;
-      r = q;
-      if (i > 0) par += g.x[i];
-    } else {
-      g.x[i] = 0;
+    for (int i = 0; i < kMaxD; ++i) {
+      if (i < d.D) {
+        g.x[i] = r & (d.dims[i] - 1);
+        r >>= d.shift[i];
+        if (i > 0) par += g.x[i];
+      } else {
+        g.x[i] = 0;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i) {
+      if (i < d.D) {
+        const int n = d.dims[i];
+        const int q = r / n;
+        g.x[i] = r - q * n;
+        r = q;
+        if (i > 0) par += g.x[i];
+      } else {
+        g.x[i] = 0;
+      }
     }
   }
   par &= 1;
@@ -97,7 +110,7 @@ template <class S>
 __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, int colour, int mu, int layer, int jj,
                                             uint32_t &nprop, uint32_t &nacc) {
   using R = typename S::R;
-  const size_t Vh = (size_t)d.Vh;
+  const int Vh = d.Vh;
   const SiteGeo g = site_of(d, layer, colour, jj);
   const int oc = colour ^ 1;
   int offp, flp;
@@ -114,18 +127,21 @@ __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, 
     const int sn = g.s + offn, ln = layer ^ fln;       // x + nu
     const int sm = g.s + offm, lm = layer ^ flm;       // x - nu
     const int spm = sp + offm, lpm = lp ^ flm;         // x + mu - nu
-    // upper staple U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
-    const M3<R> a = S::load(plane_ptr<S>(d, lp, oc, nu), Vh, sp >> 1);
-    const M3<R> b = S::load(plane_ptr<S>(d, ln, oc, mu), Vh, sn >> 1);
-    const M3<R> c = S::load(plane_ptr<S>(d, layer, colour, nu), Vh, jj);
-    const M3<R> t = mul_nd(a, b);
-    m3_acc(A, mul_nd(t, c));
-    // lower staple U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^+ U_nu(x-nu)
-    const M3<R> e = S::load(plane_ptr<S>(d, lm, oc, mu), Vh, sm >> 1);
-    const M3<R> f = S::load(plane_ptr<S>(d, lpm, colour, nu), Vh, spm >> 1);
-    const M3<R> h = S::load(plane_ptr<S>(d, lm, oc, nu), Vh, sm >> 1);
-    const M3<R> t2 = mul_nn(e, f);
-    m3_acc(A, mul_dn(t2, h));
+    // upper staple U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ = a (c b)^+, all factors SU(3):
+    // two rows of each product, the third from the cross product
+    const M3<R> b = S::load(plane_ptr<S>(d, ln, oc, mu), Vh, sn >> 1);       // U_mu(x+nu)
+    const M3<R> c = S::load2(plane_ptr<S>(d, layer, colour, nu), Vh, jj);    // U_nu(x)
+    M3<R> cb = mul_nn_2(c, b);
+    third_row(cb);
+    const M3<R> a = S::load2(plane_ptr<S>(d, lp, oc, nu), Vh, sp >> 1);      // U_nu(x+mu)
+    acc_su3_2rows(A, mul_nd_2(a, cb));
+    // lower staple U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) = (e f)^+ h
+    const M3<R> f = S::load(plane_ptr<S>(d, lpm, colour, nu), Vh, spm >> 1); // U_nu(x+mu-nu)
+    const M3<R> e = S::load2(plane_ptr<S>(d, lm, oc, mu), Vh, sm >> 1);      // U_mu(x-nu)
+    M3<R> ef = mul_nn_2(e, f);
+    third_row(ef);
+    const M3<R> h = S::load(plane_ptr<S>(d, lm, oc, nu), Vh, sm >> 1);       // U_nu(x-nu)
+    acc_su3_2rows(A, mul_dn_2(ef, h));
   }
   typename S::Vec *pu = plane_ptr<S>(d, layer, colour, mu);
   M3<R> U = S::load(pu, Vh, jj);
@@ -139,7 +155,7 @@ __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, 
 
 template <class S>
 __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int jj) {
-  const size_t Vh = (size_t)d.Vh;
+  const int Vh = d.Vh;
   for (int colour = 0; colour < 2; ++colour)
     for (int mu = 0; mu < d.D; ++mu) {
       typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
@@ -157,7 +173,7 @@ __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int j
 template <class S>
 __device__ __forceinline__ void measure_site(const ChainDesc &d, int layer, int jj, double acc[kPartVals]) {
   using R = typename S::R;
-  const size_t Vh = (size_t)d.Vh;
+  const int Vh = d.Vh;
   const int D = d.D;
   for (int colour = 0; colour < 2; ++colour) {
     const SiteGeo g = site_of(d, layer, colour, jj);
@@ -278,6 +294,21 @@ __device__ __forceinline__ void load_chain(const EngineArgs &ea, int c, ChainDes
   for (int i = threadIdx.x; i < n2; i += blockDim.x) dst2[i] = __ldcg(src2 + i);
 }
 
+// Warp-sum the FHKP counters and add them to the chain's totals.
+__device__ __forceinline__ void flush_counters(const ChainDesc &d, uint32_t &np, uint32_t &na) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    np += __shfl_down_sync(0xffffffffu, np, o);
+    na += __shfl_down_sync(0xffffffffu, na, o);
+  }
+  if ((threadIdx.x & 31) == 0 && np) {
+    atomicAdd(d.counters + 0, (unsigned long long)np);
+    atomicAdd(d.counters + 1, (unsigned long long)na);
+  }
+  np = 0;
+  na = 0;
+}
+
 // Next stage of a chain's stage machine (the host keeps an identical mirror):
 // the 2D update phases of a sweep, then a re-unitarisation and/or a
 // measurement when the completed-sweep count is a multiple of their
@@ -300,72 +331,65 @@ __device__ __host__ inline void advance_stage(const ChainDesc &d, ChainState &s)
   if (s.stage == 0 && s.sweep >= s.target) s.active = 0;
 }
 
-template <class S>
-__global__ void __launch_bounds__(256) k_tick(EngineArgs ea) {
+// Register variants of the tick kernel: __launch_bounds__(threads, CTAs per
+// SM) caps registers at 65536 / (threads x CTAs).  The autotuner times them.
+template <int V> struct TickBounds;
+template <> struct TickBounds<0> { static constexpr int kThreads = 256, kMinBlocks = 2; };  // 128 registers
+template <> struct TickBounds<1> { static constexpr int kThreads = 128, kMinBlocks = 5; };  // 96 registers
+template <> struct TickBounds<2> { static constexpr int kThreads = 128, kMinBlocks = 6; };  // 80 registers
+template <> struct TickBounds<3> { static constexpr int kThreads = 256, kMinBlocks = 1; };  // FP64: no cap
+
+template <class S, int V>
+__global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBlocks) k_tick(EngineArgs ea) {
   __shared__ ChainDesc sd;
   __shared__ ChainState ss;
-  __shared__ int s_chain;
-  __shared__ int s_last;
   __shared__ double s_red[32 * kPartVals];
-  __shared__ unsigned long long s_cnt[2];
   const int total = ea.hdr->total_tiles;
   const int tile = blockDim.x;
+  int cur = -1;
+  uint32_t np = 0, na = 0;  // FHKP counters of the current chain, flushed per warp
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
-    if (threadIdx.x == 0) {
-      s_chain = ea.tile_chain[t];
-      s_cnt[0] = 0;
-      s_cnt[1] = 0;
+    const int c = __ldg(ea.tile_chain + t);  // the same for every thread of the CTA
+    if (c != cur) {
+      if (cur >= 0) flush_counters(sd, np, na);
+      __syncthreads();  // every warp is done with the previous descriptor
+      load_chain(ea, c, sd, ss);
+      __syncthreads();
+      cur = c;
     }
-    __syncthreads();
-    load_chain(ea, s_chain, sd, ss);
-    __syncthreads();
-    if (ss.active) {
-      const int lt = t - sd.tile_base;
-      const int layer = lt / sd.tiles_per_layer;
-      const int jj = (lt - layer * sd.tiles_per_layer) * tile + threadIdx.x;
-      const bool valid = jj < sd.Vh;
-      if (ss.stage < 2 * sd.D) {
-        uint32_t np = 0, na = 0;
-        const int colour = ss.stage / sd.D, mu = ss.stage - colour * sd.D;
-        if (valid) update_site<S>(sd, ss.sweep, colour, mu, layer, jj, np, na);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          np += __shfl_down_sync(0xffffffffu, np, o);
-          na += __shfl_down_sync(0xffffffffu, na, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-          atomicAdd(&s_cnt[0], (unsigned long long)np);
-          atomicAdd(&s_cnt[1], (unsigned long long)na);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          atomicAdd(sd.counters + 0, s_cnt[0]);
-          atomicAdd(sd.counters + 1, s_cnt[1]);
-        }
-      } else if (ss.stage == kStageReunit) {
-        if (valid) reunit_site<S>(sd, layer, jj);
-      } else {
-        double v[kPartVals] = {0, 0, 0, 0};
-        if (valid) measure_site<S>(sd, layer, jj, v);
-        block_reduce(v, s_red);
-        if (threadIdx.x == 0)
-          for (int k = 0; k < kPartVals; ++k) sd.partials[(size_t)lt * kPartVals + k] = v[k];
-      }
+    if (!ss.active) continue;
+    const int lt = t - sd.tile_base;
+    const int layer = lt / sd.tiles_per_layer;
+    const int jj = (lt - layer * sd.tiles_per_layer) * tile + threadIdx.x;
+    const bool valid = jj < sd.Vh;
+    if (ss.stage < 2 * sd.D) {
+      const int colour = ss.stage / sd.D, mu = ss.stage - colour * sd.D;
+      if (valid) update_site<S>(sd, ss.sweep, colour, mu, layer, jj, np, na);
+    } else if (ss.stage == kStageReunit) {
+      if (valid) reunit_site<S>(sd, layer, jj);
+    } else {
+      double v[kPartVals] = {0, 0, 0, 0};
+      if (valid) measure_site<S>(sd, layer, jj, v);
+      block_reduce(v, s_red);
+      if (threadIdx.x == 0)
+        for (int k = 0; k < kPartVals; ++k) sd.partials[(size_t)lt * kPartVals + k] = v[k];
     }
-    __syncthreads();
   }
-  // The last CTA advances the stage machines and finishes measurements.
-  if (threadIdx.x == 0) {
+  if (cur >= 0) flush_counters(sd, np, na);
+  // The last warp of the grid to finish advances the stage machines and
+  // finishes measurements.  Counting warps, not CTAs, lets a warp leave as
+  // soon as its own work is done (no CTA-wide barrier at the end).
+  const int lane = threadIdx.x & 31;
+  unsigned prev = 0;
+  if (lane == 0) {
     __threadfence();
-    const unsigned prev = atomicAdd(&ea.hdr->done_ctas, 1u);
-    s_last = (prev == gridDim.x - 1);
+    prev = atomicAdd(&ea.hdr->done_warps, 1u);
   }
-  __syncthreads();
-  if (!s_last) return;
+  prev = __shfl_sync(0xffffffffu, prev, 0);
+  if (prev != gridDim.x * (blockDim.x >> 5) - 1) return;
   __threadfence();
   const int nchains = ea.hdr->nchains;
-  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int c = warp; c < nchains; c += nwarps) {
+  for (int c = 0; c < nchains; ++c) {
     const ChainState st = ea.state[c];
     if (st.active && st.stage == kStageMeasure) {
       const ChainDesc &d = ea.desc[c];
@@ -373,15 +397,16 @@ __global__ void __launch_bounds__(256) k_tick(EngineArgs ea) {
       finalize_measure(d, d.partials, out);
     }
   }
-  __syncthreads();
-  for (int c = threadIdx.x; c < nchains; c += blockDim.x) {
+  __syncwarp();
+  __threadfence();
+  for (int c = lane; c < nchains; c += 32) {
     ChainState st = ea.state[c];
     if (!st.active) continue;
     if (st.stage == kStageMeasure) st.n_meas += 1;
     advance_stage(ea.desc[c], st);
     ea.state[c] = st;
   }
-  if (threadIdx.x == 0) ea.hdr->done_ctas = 0;
+  if (lane == 0) ea.hdr->done_warps = 0;
 }
 
 // ------------------------------------------------------------------ stand-alone measurement
@@ -449,7 +474,7 @@ __global__ void k_start(ChainDesc *desc_dev, int hot) {
       }
       reunit_d(m);
     }
-    S::store(plane_ptr<S>(d, layer, colour, mu), (size_t)d.Vh, jj, m3_cast<typename S::R>(m));
+    S::store(plane_ptr<S>(d, layer, colour, mu), d.Vh, jj, m3_cast<typename S::R>(m));
   }
 }
 
@@ -475,7 +500,7 @@ __global__ void k_convert(ChainDesc *desc_dev, double *canon, int to_canonical) 
     typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
     double *c = canon + i * 18;
     if (to_canonical) {
-      const M3<typename S::R> m = S::load(p, (size_t)d.Vh, s >> 1);
+      const M3<typename S::R> m = S::load(p, d.Vh, s >> 1);
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
           c[(a * 3 + b) * 2] = (double)m.e[a][b].re;
@@ -485,21 +510,32 @@ __global__ void k_convert(ChainDesc *desc_dev, double *canon, int to_canonical) 
       M3<typename S::R> m;
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) m.e[a][b] = {(typename S::R)c[(a * 3 + b) * 2], (typename S::R)c[(a * 3 + b) * 2 + 1]};
-      S::store(p, (size_t)d.Vh, s >> 1, m);
+      S::store(p, d.Vh, s >> 1, m);
     }
   }
 }
 
 // ------------------------------------------------------------------ launchers
 
-template <class S>
-static cudaError_t launch_tick_t(const EngineArgs &ea, int grid, int block, cudaStream_t st) {
-  k_tick<S><<<grid, block, 0, st>>>(ea);
-  return cudaGetLastError();
+int tick_variants(int storage) { return storage == 0 ? 1 : 3; }
+
+int tick_max_threads(int storage, int variant) {
+  if (storage == 0) return TickBounds<3>::kThreads;
+  return variant == 0 ? TickBounds<0>::kThreads : (variant == 1 ? TickBounds<1>::kThreads : TickBounds<2>::kThreads);
 }
 
-cudaError_t launch_tick(int storage, const EngineArgs &ea, int grid, int block, cudaStream_t st) {
-  return storage == 0 ? launch_tick_t<StoreF64x18>(ea, grid, block, st) : launch_tick_t<StoreF32x12>(ea, grid, block, st);
+cudaError_t launch_tick(int storage, int variant, const EngineArgs &ea, int grid, int block, cudaStream_t st) {
+  if (block > tick_max_threads(storage, variant)) return cudaErrorInvalidConfiguration;
+  if (storage == 0) {
+    k_tick<StoreF64x18, 3><<<grid, block, 0, st>>>(ea);
+  } else if (variant == 0) {
+    k_tick<StoreF32x12, 0><<<grid, block, 0, st>>>(ea);
+  } else if (variant == 1) {
+    k_tick<StoreF32x12, 1><<<grid, block, 0, st>>>(ea);
+  } else {
+    k_tick<StoreF32x12, 2><<<grid, block, 0, st>>>(ea);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st) {
@@ -533,9 +569,14 @@ cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, doub
   return cudaGetLastError();
 }
 
-cudaError_t tick_occupancy(int storage, int block, int *ctas_per_sm) {
-  if (storage == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF64x18>, block, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF32x12>, block, 0);
+cudaError_t tick_occupancy(int storage, int variant, int block, int *ctas_per_sm) {
+  *ctas_per_sm = 0;
+  if (block > tick_max_threads(storage, variant)) return cudaSuccess;
+  if (storage == 0)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF64x18, 3>, block, 0);
+  if (variant == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF32x12, 0>, block, 0);
+  if (variant == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF32x12, 1>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF32x12, 2>, block, 0);
 }
 
 void host_advance_stage(const ChainDesc &d, ChainState &s) { advance_stage(d, s); }

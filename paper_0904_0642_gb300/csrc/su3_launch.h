@@ -7,12 +7,16 @@
 namespace su3g {
 
 // storage: 0 = FP64 18-real, 1 = FP32 12-real.
-cudaError_t launch_tick(int storage, const EngineArgs &ea, int grid, int block, cudaStream_t st);
+// The tick kernel comes in register variants (FP32: 0 = 128, 1 = 96, 2 = 80
+// registers; FP64: one); a variant limits the CTA width to tick_max_threads.
+int tick_variants(int storage);
+int tick_max_threads(int storage, int variant);
+cudaError_t launch_tick(int storage, int variant, const EngineArgs &ea, int grid, int block, cudaStream_t st);
 cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st);
 cudaError_t launch_start(int storage, ChainDesc *desc_dev, size_t nlinks, int hot, cudaStream_t st);
 cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, double *canon, int to_canonical,
                            cudaStream_t st);
-cudaError_t tick_occupancy(int storage, int block, int *ctas_per_sm);
+cudaError_t tick_occupancy(int storage, int variant, int block, int *ctas_per_sm);
 void host_advance_stage(const ChainDesc &d, ChainState &s);
 
 }  // namespace su3g

@@ -63,11 +63,14 @@ def test_graph_and_launch_shape_do_not_change_links(storage):
     ref.use_graph(False)
     ref.sweep(7)
     want = ref.get_links()
-    for threads, ctas in [(32, 1), (64, 0), (128, 2), (256, 0)]:
+    shapes = [(0, 32, 1), (0, 64, 0), (0, 128, 2), (0, 256, 0)]
+    if storage == su3.SU3_FP32_12:
+        shapes += [(1, 128, 0), (2, 96, 3), (2, 128, 1)]
+    for variant, threads, ctas in shapes:
         lat = su3.Lattice(dims, **kw)
-        lat.set_launch(threads, ctas)
+        lat.set_launch(threads, ctas, variant=variant)
         lat.sweep(7)
-        assert np.array_equal(lat.get_links(), want), (threads, ctas)
+        assert np.array_equal(lat.get_links(), want), (variant, threads, ctas)
         assert lat.stats() == ref.stats()
 
 
