@@ -192,6 +192,42 @@ typedef struct su3_profile {
 su3_status su3_set_profiling(su3_lattice *lat, int on);
 su3_status su3_get_profile(su3_lattice *lat, su3_profile *out, int reset);
 
+/* ---------------------------------------------------------------- measurement without allocation
+ * The paper has no counterpart to this call; it exists for users of the
+ * library.
+ *
+ * su3_measure_noalloc computes what su3_measure_async computes (plaquette
+ * total / space / time and Polyakov loop, per layer and for the whole
+ * lattice) for links the caller already holds on the device, and allocates
+ * no memory at all, device or host.  It is for callers that cannot call
+ * cudaMalloc: code embedded in a host framework whose memory pool must stay
+ * the only owner of device memory, loops that cannot take the device-wide
+ * synchronisation an allocation may cause, and plug-ins that run under a
+ * fixed device-memory budget.
+ *
+ * cfg:        geometry and storage of the links (D, dims, boundary,
+ *             glue_mask, storage); the other fields are ignored.
+ * links:      device pointer to link storage in the library's layout,
+ *             16-byte aligned (e.g. the caller-owned link_buffer a lattice
+ *             was created with).
+ * device_out: device pointer to 5*(layers+1) doubles, written as
+ *             [total, space, time, poly_re, poly_im] for each layer, then for
+ *             the whole lattice.
+ * stream:     cudaStream_t (NULL: the legacy default stream); asynchronous.
+ *
+ * Scratch: the per-block partial sums go to a fixed 1 MiB array inside the
+ * library (32768 slots, one per 256 sites of one colour and layer), which
+ * every GPU that loads the library holds until the process exits.  A lattice
+ * that needs more slots (more than 8,388,608 sites of one colour summed over
+ * its layers) is rejected with SU3_EINVAL before anything is launched.  Each
+ * call writes every slot it reads, so nothing needs clearing between calls,
+ * but all calls share the one array: calls that overlap on the GPU (other
+ * streams, other threads) race, so serialise them.
+ * Set-up: the first call on each device looks up the device address of the
+ * array (cudaGetSymbolAddress) and keeps it; make that first call on a
+ * device before any stream capture. */
+su3_status su3_measure_noalloc(const su3_config *cfg, const void *links, double *device_out, void *stream);
+
 /* ---------------------------------------------------------------- ensembles
  * Many independent chains (each with its own extents, boundary, beta, seed
  * and hits; one storage for all) advanced together: one fused persistent

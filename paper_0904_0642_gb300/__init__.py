@@ -39,7 +39,7 @@ EXPORTED = [
     "su3_ensemble_measure", "su3_ensemble_get_links", "su3_ensemble_measurements", "su3_ensemble_set_launch", "su3_ensemble_autotune", "su3_ensemble_use_graph",
     "su3_ensemble_set_profiling", "su3_ensemble_get_profile",
     "su3_server_create", "su3_server_submit", "su3_server_poll", "su3_server_wait", "su3_server_load",
-    "su3_server_destroy", "su3_last_error", "su3_version",
+    "su3_server_destroy", "su3_last_error", "su3_version", "su3_measure_noalloc",
 ]
 
 
@@ -132,6 +132,7 @@ def lib():
             "su3_server_destroy": (None, [vp]),
             "su3_last_error": (c_char_p, []),
             "su3_version": (c_char_p, []),
+            "su3_measure_noalloc": (c_int, [POINTER(su3_config), vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -268,6 +269,12 @@ def su3_get_profile(h, reset: bool = False) -> dict:
     p = su3_profile()
     _check(lib().su3_get_profile(h, byref(p), int(bool(reset))))
     return {k: getattr(p, k) for k, _ in su3_profile._fields_}
+
+
+def su3_measure_noalloc(cfg: su3_config, links_ptr: int, device_out_ptr: int, stream=None):
+    """Measure links the caller holds on the device without any allocation
+    (for callers that cannot call cudaMalloc); see include/su3.h."""
+    _check(lib().su3_measure_noalloc(byref(cfg), links_ptr, device_out_ptr, _stream_handle(stream)))
 
 
 def su3_last_error() -> str:

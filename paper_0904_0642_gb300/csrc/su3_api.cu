@@ -912,6 +912,28 @@ extern "C" su3_status su3_autotune(su3_lattice *lat, int *variant, int *threads,
   return autotune_engine(lat->eng, variant, threads, ctas_per_sm, us_per_sweep);
 }
 
+// ------------------------------------------------------------------ measurement without allocation
+
+extern "C" su3_status su3_measure_noalloc(const su3_config *cfg, const void *links, double *device_out,
+                                          void *stream) {
+  TRY(validate(cfg));
+  if (!links || ((uintptr_t)links & 15)) return fail(SU3_EINVAL, "links must be a 16-byte aligned device pointer");
+  if (!device_out) return fail(SU3_EINVAL, "device_out is NULL");
+  const int block = 256;
+  Chain ch;  // a descriptor only: no device memory is touched or allocated here
+  ch.cfg = *cfg;
+  ch.links = const_cast<void *>(links);
+  fill_desc(ch, block);
+  const long long tiles = (long long)ch.desc.tiles_per_layer * ch.desc.nlayers;
+  if (tiles > noalloc_max_tiles())
+    return fail(SU3_EINVAL,
+                "lattice needs %lld partial-sum slots (one per %d sites of a colour), the static scratch holds %d "
+                "(1 MiB); use su3_plaquette / su3_measure_async instead",
+                tiles, block, noalloc_max_tiles());
+  CU(launch_measure_noalloc(cfg->storage, ch.desc, block, device_out, (cudaStream_t)stream));
+  return SU3_OK;
+}
+
 // ------------------------------------------------------------------ ensembles
 
 struct su3_ensemble {

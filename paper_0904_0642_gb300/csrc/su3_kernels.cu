@@ -9,6 +9,7 @@
 // k_start, k_convert, k_measure*: start configurations, canonical-layout
 //   conversion and stand-alone measurements.
 #include <cstdio>
+#include <mutex>
 
 #include "su3_device.cuh"
 #include "su3_launch.h"
@@ -513,6 +514,72 @@ __global__ void k_convert(ChainDesc *desc_dev, double *canon, int to_canonical) 
       S::store(p, d.Vh, s >> 1, m);
     }
   }
+}
+
+// ------------------------------------------------------------------ measurement without allocation
+// For callers that cannot allocate device memory (see su3_measure_noalloc):
+// the per-tile partial sums go to a fixed array in the library's own device
+// memory instead of a buffer from cudaMalloc.  Every tile writes its own
+// slots before the finishing kernel reads them, so nothing has to start at
+// zero; calls that overlap on the GPU share the array and race.
+
+constexpr int kNoAllocTiles = 32768;  // 32768 tiles x 4 doubles = 1 MiB
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocTiles * kPartVals];
+
+template <class S>
+__global__ void __launch_bounds__(256) k_measure_noalloc(ChainDesc d, double *partials) {
+  __shared__ double s_red[32 * kPartVals];
+  const int total = d.tiles_per_layer * d.nlayers;
+  for (int lt = blockIdx.x; lt < total; lt += gridDim.x) {
+    const int layer = lt / d.tiles_per_layer;
+    const int jj = (lt - layer * d.tiles_per_layer) * blockDim.x + threadIdx.x;
+    double v[kPartVals] = {0, 0, 0, 0};
+    if (jj < d.Vh) measure_site<S>(d, layer, jj, v);
+    block_reduce(v, s_red);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < kPartVals; ++k) partials[(size_t)lt * kPartVals + k] = v[k];
+  }
+}
+
+__global__ void k_measure_finalize_noalloc(ChainDesc d, const double *partials, double *out) {
+  finalize_measure(d, partials, out);
+}
+
+int noalloc_max_tiles() { return kNoAllocTiles; }
+
+// Device address of the scratch array on the current device.  Host code
+// cannot use the symbol itself (it names a host-side stand-in), so the
+// address is looked up once per device and cached.
+static cudaError_t noalloc_scratch(double **ptr) {
+  static std::mutex mu;
+  static double *addr[64] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    addr[dev] = static_cast<double *>(p);
+  }
+  *ptr = addr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_measure_noalloc(int storage, const ChainDesc &d, int block, double *out, cudaStream_t st) {
+  double *partials = nullptr;
+  cudaError_t e = noalloc_scratch(&partials);
+  if (e != cudaSuccess) return e;
+  const int tiles = d.tiles_per_layer * d.nlayers;
+  const int grid = tiles < 4096 ? tiles : 4096;
+  if (storage == 0)
+    k_measure_noalloc<StoreF64x18><<<grid, block, 0, st>>>(d, partials);
+  else
+    k_measure_noalloc<StoreF32x12><<<grid, block, 0, st>>>(d, partials);
+  k_measure_finalize_noalloc<<<1, 32, 0, st>>>(d, partials, out);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ launchers

@@ -18,5 +18,9 @@ cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, doub
                            cudaStream_t st);
 cudaError_t tick_occupancy(int storage, int variant, int block, int *ctas_per_sm);
 void host_advance_stage(const ChainDesc &d, ChainState &s);
+// Measurement with partial sums in the library's static device scratch
+// (su3_measure_noalloc); the descriptor is passed by value.
+int noalloc_max_tiles();
+cudaError_t launch_measure_noalloc(int storage, const ChainDesc &d, int block, double *out, cudaStream_t st);
 
 }  // namespace su3g
