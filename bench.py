@@ -188,6 +188,147 @@ def cpu_baseline():
             "seconds": dt}
 
 
+# ---------------------------------------------------------------- other workloads
+# Each is reported as an extra key of the bench line (same JSON line).
+
+
+def bench_ensemble(su3, torch, stream):
+    """256 independent 8^4 chains, beta_c ~ U[5.5, 6.5], FP32, one fused
+    persistent launch per phase, graph-captured, autotuned; against the same
+    chains swept one after another as single-chain lattices."""
+    import numpy as np
+    rng = np.random.default_rng(2009)
+    betas = rng.uniform(5.5, 6.5, 256)
+    sweeps = 200
+    cfgs = [su3.make_config([8, 8, 8, 8], beta=float(b), seed=5000 + c, storage=su3.SU3_FP32_12,
+                            start=su3.SU3_START_HOT, hits=HITS, reunit_every=10) for c, b in enumerate(betas)]
+    ens = su3.Ensemble(cfgs, stream=stream)
+    var, thr, ctas, _ = ens.autotune()
+    ens.sweep(3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ens.sweep(sweeps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ens = e0.elapsed_time(e1) * 1e-3
+    links = 256 * 8 ** 4 * 4
+    # 256 sequential single-chain runs (fewer sweeps each, same per-sweep work)
+    seq_sweeps = 20
+    lats = [su3.Lattice([8, 8, 8, 8], beta=float(b), seed=5000 + c, storage=su3.SU3_FP32_12,
+                        start=su3.SU3_START_HOT, hits=HITS, reunit_every=10, stream=stream)
+            for c, b in enumerate(betas)]
+    for lat in lats:
+        lat.sweep(1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for lat in lats:
+        lat.sweep(seq_sweeps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) * 1e-3
+    for lat in lats:
+        lat.close()
+    meas = ens.measure()
+    ens.close()
+    fused = sweeps * links / t_ens
+    seq = seq_sweeps * links / t_seq
+    return {"workload": "256 chains of 8^4 PBC, beta ~ U[5.5,6.5], FP32, 200 sweeps, fused + graph",
+            "value": fused, "unit": UNIT, "sequential_single_chain": seq, "speedup": fused / seq,
+            "launch": {"variant": var, "threads": thr, "ctas_per_sm": ctas},
+            "plaquette_mean": float(meas[:, 0].mean())}
+
+
+def bench_dlt_and_d3(su3, torch, stream):
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, kw, sweeps in (
+            ("dlt_2x16^3x4_time_glued_b5.7", dict(dims=[16, 16, 16, 4], boundary=su3.SU3_DLT, glue_mask=0b1000,
+                                                   beta=5.7), 500),
+            ("pbc_64^3_d3_b10", dict(dims=[64, 64, 64], beta=10.0), 500)):
+        lat = su3.Lattice(storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT, seed=SEED, hits=HITS, reunit_every=10,
+                          stream=stream, **kw)
+        var, thr, ctas, _ = lat.autotune()
+        lat.sweep(5)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.sweep(sweeps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        rec = {"value": sweeps * lat.nlinks / t, "unit": UNIT, "sweeps": sweeps, "links": lat.nlinks,
+               "launch": {"variant": var, "threads": thr, "ctas_per_sm": ctas}}
+        for layer in range(lat.nlayers):
+            p = lat.plaquette(layer)
+            q = lat.polyakov(layer)
+            rec[f"layer{layer}"] = {"plaquette": p[0], "space": p[1], "time": p[2], "polyakov": [q.real, q.imag]}
+        out[name] = rec
+        lat.close()
+    return out
+
+
+def bench_serving(su3, torch, n_jobs=60, n_fp64=8):
+    """Poisson arrivals (50 jobs/s) of mixed jobs into the continuous-batching
+    server; p50/p99 latency and throughput, against a plain FP64
+    one-job-at-a-time loop over the first n_fp64 jobs (its latencies come
+    from the same arrival times with FIFO service)."""
+    import numpy as np
+    rng = np.random.default_rng(50)
+    shapes = [[8, 8, 8, 8], [12, 12, 12, 12], [16, 16, 16, 4], [24, 24, 24, 24], [32, 32, 32, 8], [48, 48, 48]]
+    jobs = []
+    t = 0.0
+    for j in range(n_jobs):
+        t += rng.exponential(1 / 50.0)
+        dims = shapes[rng.integers(len(shapes))]
+        boundary = su3.SU3_DLT if rng.random() < 0.2 else su3.SU3_PBC
+        jobs.append((t, dims, boundary, float(rng.uniform(5.6, 6.4)), int(rng.integers(50, 501)), 7000 + j))
+
+    def links_of(dims, boundary):
+        return int(np.prod(dims)) * len(dims) * (2 if boundary == su3.SU3_DLT else 1)
+
+    srv = su3.Server(max_slots=64)
+    t0 = time.perf_counter()
+    ids = []
+    for (ta, dims, b, beta, sw, seed) in jobs:
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        cfg = su3.make_config(dims, boundary=b, beta=beta, seed=seed, storage=su3.SU3_FP32_12,
+                              start=su3.SU3_START_HOT, hits=HITS, reunit_every=10)
+        ids.append((srv.submit(cfg, sw), time.perf_counter() - t0))
+    lat_s = []
+    for (jid, tsub), (ta, dims, b, beta, sw, seed) in zip(ids, jobs):
+        r = srv.wait(jid, timeout_s=600)
+        lat_s.append(r.finish_s - r.submit_s)
+    t_all = time.perf_counter() - t0
+    srv.close()
+    total_updates = sum(links_of(d, b) * sw for (_, d, b, _, sw, _) in jobs)
+    # plain FP64 one job at a time, FIFO over the same arrival times
+    service = []
+    for (ta, dims, b, beta, sw, seed) in jobs[:n_fp64]:
+        lat = su3.Lattice(dims, boundary=b, beta=beta, seed=seed, storage=su3.SU3_FP64_18, start=su3.SU3_START_HOT,
+                          hits=HITS, reunit_every=10)
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        lat.sweep(sw)
+        lat.plaquette()
+        service.append(time.perf_counter() - s0)
+        lat.close()
+    free_at, lat64 = 0.0, []
+    for (ta, *_), sv in zip(jobs[:n_fp64], service):
+        start = max(ta, free_at)
+        free_at = start + sv
+        lat64.append(free_at - ta)
+    return {"workload": f"{n_jobs} Poisson jobs (50/s), shapes 8^4..48^3, 20% DLT, 50-500 sweeps, FP32 + FP64 "
+                        "reunitarize/reductions",
+            "jobs_per_s": n_jobs / t_all, "link_updates_per_s": total_updates / t_all,
+            "latency_p50_s": float(np.percentile(lat_s, 50)), "latency_p99_s": float(np.percentile(lat_s, 99)),
+            "fp64_one_at_a_time": {"jobs": n_fp64, "latency_p50_s": float(np.percentile(lat64, 50)),
+                                   "latency_p99_s": float(np.percentile(lat64, 99)),
+                                   "link_updates_per_s": sum(links_of(d, b) * sw for (_, d, b, _, sw, _) in
+                                                             jobs[:n_fp64]) / sum(service)}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,6 +472,10 @@ def main():
         line["plaquette_fp32_vs_fp64_after_10_sweeps"] = {"fp32": p32, "fp64": p64, "abs_diff": abs(p32 - p64)}
         ref32.close()
         lat64.close()
+        if rank == 0 and world == 1:
+            line["ensemble_256x8^4"] = bench_ensemble(su3, torch, stream)
+            line.update(bench_dlt_and_d3(su3, torch, stream))
+            line["serving"] = bench_serving(su3, torch)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -188,6 +188,7 @@ static void fill_desc(Chain &ch, int tile) {
       while ((1 << d.shift[i]) < c.dims[i]) ++d.shift[i];
     }
   }
+
   d.beta_f = (float)c.beta;
   d.beta_d = c.beta;
 }

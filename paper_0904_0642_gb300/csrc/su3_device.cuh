@@ -418,14 +418,18 @@ __device__ __forceinline__ bool su2_draw(float alpha, int hits, uint2 key, uint3
     for (int i = 0; i < 4; ++i) x[i] = (float)xd[i];
     return a;
   }
+  // The float draw uses the SFU forms of ln, sin and cos: their absolute
+  // errors (~2e-7 for ln, ~4e-7 for sin/cos on [-pi, pi]) stay well inside
+  // the FP32 storage rounding of the updated link.  Angles 2 pi u are taken
+  // as 2 pi (u - 1/2) - the sign flip is absorbed - to stay on [-pi, pi].
   float X = 0.0f;
   bool acc = false;
   const float ia = 1.0f / alpha;
   for (int h = 0; h < hits; ++h) {
     const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | (uint32_t)h, kPurposeHeatbath), key);
     ++nprop;
-    const float cs = cospif(2.0f * unif_f(w.y));
-    X = -(logf(unif_f(w.x)) + cs * cs * logf(unif_f(w.z))) * ia;
+    const float cs = __cosf(__fmaf_rn(unif_f(w.y), 6.28318530717958648f, -3.14159265358979324f));
+    X = -(__logf(unif_f(w.x)) + cs * cs * __logf(unif_f(w.z))) * ia;
     const float u4 = unif_f(w.w);
     if (u4 * u4 <= 1.0f - 0.5f * X) {
       acc = true;
@@ -437,7 +441,9 @@ __device__ __forceinline__ bool su2_draw(float alpha, int hits, uint2 key, uint3
   const float costh = 2.0f * unif_f(w.x) - 1.0f;
   const float sinth = sqrtf(1.0f - costh * costh);
   float sphi, cphi;
-  sincospif(2.0f * unif_f(w.y), &sphi, &cphi);
+  __sincosf(__fmaf_rn(unif_f(w.y), 6.28318530717958648f, -3.14159265358979324f), &sphi, &cphi);
+  sphi = -sphi;  // sin(2 pi u) = -sin(2 pi (u - 1/2)), likewise cos
+  cphi = -cphi;
   const float rho = sqrtf(X * (2.0f - X));
   x[0] = 1.0f - X;
   x[1] = rho * sinth * cphi;

@@ -107,42 +107,56 @@ __device__ __forceinline__ int sel(const int (&x)[kMaxD], int i) {
 
 // ------------------------------------------------------------------ one link update
 
+// The staples of one direction nu added to A.
 template <class S>
+__device__ __forceinline__ void add_staples(const ChainDesc &d, const SiteGeo &g, int colour, int mu, int nu, int xnu,
+                                            int sp, int lp, M3<typename S::R> &A) {
+  using R = typename S::R;
+  const int Vh = d.Vh, layer = g.layer, jj = g.s >> 1, oc = colour ^ 1;
+  int offn, fln, offm, flm;
+  step_fwd(d, xnu, nu, offn, fln);
+  step_bwd(d, xnu, nu, offm, flm);
+  const int sn = g.s + offn, ln = layer ^ fln;       // x + nu
+  const int sm = g.s + offm, lm = layer ^ flm;       // x - nu
+  const int spm = sp + offm, lpm = lp ^ flm;         // x + mu - nu
+  // upper staple U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ = a (c b)^+, all factors SU(3):
+  // two rows of each product, the third from the cross product
+  const M3<R> b = S::load(plane_ptr<S>(d, ln, oc, mu), Vh, sn >> 1);       // U_mu(x+nu)
+  const M3<R> c = S::load2(plane_ptr<S>(d, layer, colour, nu), Vh, jj);    // U_nu(x)
+  M3<R> cb = mul_nn_2(c, b);
+  third_row(cb);
+  const M3<R> a = S::load2(plane_ptr<S>(d, lp, oc, nu), Vh, sp >> 1);      // U_nu(x+mu)
+  acc_su3_2rows(A, mul_nd_2(a, cb));
+  // lower staple U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) = (e f)^+ h
+  const M3<R> f = S::load(plane_ptr<S>(d, lpm, colour, nu), Vh, spm >> 1); // U_nu(x+mu-nu)
+  const M3<R> e = S::load2(plane_ptr<S>(d, lm, oc, mu), Vh, sm >> 1);      // U_mu(x-nu)
+  M3<R> ef = mul_nn_2(e, f);
+  third_row(ef);
+  const M3<R> h = S::load(plane_ptr<S>(d, lm, oc, nu), Vh, sm >> 1);       // U_nu(x-nu)
+  acc_su3_2rows(A, mul_dn_2(ef, h));
+}
+
+// ROLLED: the loop over staple directions stays a loop (no unrolling), so the
+// compiler cannot hoist later directions' loads; fewer registers, less code.
+template <class S, bool ROLLED>
 __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, int colour, int mu, int layer, int jj,
                                             uint32_t &nprop, uint32_t &nacc) {
   using R = typename S::R;
   const int Vh = d.Vh;
   const SiteGeo g = site_of(d, layer, colour, jj);
-  const int oc = colour ^ 1;
   int offp, flp;
   step_fwd(d, sel(g.x, mu), mu, offp, flp);
   const int sp = g.s + offp, lp = layer ^ flp;  // x + mu
 
   M3<R> A = m3_zero<R>();
+  if constexpr (ROLLED) {
+#pragma unroll 1
+    for (int nu = 0; nu < d.D; ++nu)
+      if (nu != mu) add_staples<S>(d, g, colour, mu, nu, sel(g.x, nu), sp, lp, A);
+  } else {
 #pragma unroll
-  for (int nu = 0; nu < kMaxD; ++nu) {
-    if (nu >= d.D || nu == mu) continue;
-    int offn, fln, offm, flm;
-    step_fwd(d, g.x[nu], nu, offn, fln);
-    step_bwd(d, g.x[nu], nu, offm, flm);
-    const int sn = g.s + offn, ln = layer ^ fln;       // x + nu
-    const int sm = g.s + offm, lm = layer ^ flm;       // x - nu
-    const int spm = sp + offm, lpm = lp ^ flm;         // x + mu - nu
-    // upper staple U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ = a (c b)^+, all factors SU(3):
-    // two rows of each product, the third from the cross product
-    const M3<R> b = S::load(plane_ptr<S>(d, ln, oc, mu), Vh, sn >> 1);       // U_mu(x+nu)
-    const M3<R> c = S::load2(plane_ptr<S>(d, layer, colour, nu), Vh, jj);    // U_nu(x)
-    M3<R> cb = mul_nn_2(c, b);
-    third_row(cb);
-    const M3<R> a = S::load2(plane_ptr<S>(d, lp, oc, nu), Vh, sp >> 1);      // U_nu(x+mu)
-    acc_su3_2rows(A, mul_nd_2(a, cb));
-    // lower staple U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) = (e f)^+ h
-    const M3<R> f = S::load(plane_ptr<S>(d, lpm, colour, nu), Vh, spm >> 1); // U_nu(x+mu-nu)
-    const M3<R> e = S::load2(plane_ptr<S>(d, lm, oc, mu), Vh, sm >> 1);      // U_mu(x-nu)
-    M3<R> ef = mul_nn_2(e, f);
-    third_row(ef);
-    const M3<R> h = S::load(plane_ptr<S>(d, lm, oc, nu), Vh, sm >> 1);       // U_nu(x-nu)
-    acc_su3_2rows(A, mul_dn_2(ef, h));
+    for (int nu = 0; nu < kMaxD; ++nu)
+      if (nu < d.D && nu != mu) add_staples<S>(d, g, colour, mu, nu, g.x[nu], sp, lp, A);
   }
   typename S::Vec *pu = plane_ptr<S>(d, layer, colour, mu);
   M3<R> U = S::load(pu, Vh, jj);
@@ -334,11 +348,17 @@ __device__ __host__ inline void advance_stage(const ChainDesc &d, ChainState &s)
 
 // Register variants of the tick kernel: __launch_bounds__(threads, CTAs per
 // SM) caps registers at 65536 / (threads x CTAs).  The autotuner times them.
+// (Measured on the 32^4 workload: 80-register variants spill into L1 and lose
+// 4x; so do variants that prefetch the next staple direction into L1.)
+// kRolled: the update keeps its loop over staple directions rolled.
+// (Also measured and dropped: staging the staple links in shared memory with
+// cp.async - its 624 B per thread leave too few warps per SM.)
 template <int V> struct TickBounds;
-template <> struct TickBounds<0> { static constexpr int kThreads = 256, kMinBlocks = 2; };  // 128 registers
-template <> struct TickBounds<1> { static constexpr int kThreads = 128, kMinBlocks = 5; };  // 96 registers
-template <> struct TickBounds<2> { static constexpr int kThreads = 128, kMinBlocks = 6; };  // 80 registers
-template <> struct TickBounds<3> { static constexpr int kThreads = 256, kMinBlocks = 1; };  // FP64: no cap
+template <> struct TickBounds<0> { static constexpr int kThreads = 256, kMinBlocks = 2; static constexpr bool kRolled = false; };   // FP32, 128 regs
+template <> struct TickBounds<1> { static constexpr int kThreads = 128, kMinBlocks = 5; static constexpr bool kRolled = false; };   // FP32, 96 regs
+template <> struct TickBounds<2> { static constexpr int kThreads = 128, kMinBlocks = 5; static constexpr bool kRolled = true; };    // FP32, rolled, 96 regs
+template <> struct TickBounds<3> { static constexpr int kThreads = 256, kMinBlocks = 2; static constexpr bool kRolled = true; };    // FP32, rolled, 128 regs
+template <> struct TickBounds<10> { static constexpr int kThreads = 256, kMinBlocks = 1; static constexpr bool kRolled = false; };  // FP64
 
 template <class S, int V>
 __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBlocks) k_tick(EngineArgs ea) {
@@ -346,7 +366,6 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
   __shared__ ChainState ss;
   __shared__ double s_red[32 * kPartVals];
   const int total = ea.hdr->total_tiles;
-  const int tile = blockDim.x;
   int cur = -1;
   uint32_t np = 0, na = 0;  // FHKP counters of the current chain, flushed per warp
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -361,11 +380,11 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
     if (!ss.active) continue;
     const int lt = t - sd.tile_base;
     const int layer = lt / sd.tiles_per_layer;
-    const int jj = (lt - layer * sd.tiles_per_layer) * tile + threadIdx.x;
+    const int jj = (lt - layer * sd.tiles_per_layer) * blockDim.x + threadIdx.x;
     const bool valid = jj < sd.Vh;
     if (ss.stage < 2 * sd.D) {
       const int colour = ss.stage / sd.D, mu = ss.stage - colour * sd.D;
-      if (valid) update_site<S>(sd, ss.sweep, colour, mu, layer, jj, np, na);
+      if (valid) update_site<S, TickBounds<V>::kRolled>(sd, ss.sweep, colour, mu, layer, jj, np, na);
     } else if (ss.stage == kStageReunit) {
       if (valid) reunit_site<S>(sd, layer, jj);
     } else {
@@ -584,25 +603,44 @@ cudaError_t launch_measure_noalloc(int storage, const ChainDesc &d, int block, d
 
 // ------------------------------------------------------------------ launchers
 
-int tick_variants(int storage) { return storage == 0 ? 1 : 3; }
+int tick_variants(int storage) { return storage == 0 ? 1 : 4; }
+
+template <int V>
+static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_t st) {
+  if constexpr (V == 10)
+    k_tick<StoreF64x18, 10><<<grid, block, 0, st>>>(ea);
+  else
+    k_tick<StoreF32x12, V><<<grid, block, 0, st>>>(ea);
+  return cudaGetLastError();
+}
+
+template <int V>
+static cudaError_t occ_v(int block, int *ctas) {
+  if constexpr (V == 10)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF64x18, 10>, block, 0);
+  else
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF32x12, V>, block, 0);
+}
 
 int tick_max_threads(int storage, int variant) {
-  if (storage == 0) return TickBounds<3>::kThreads;
-  return variant == 0 ? TickBounds<0>::kThreads : (variant == 1 ? TickBounds<1>::kThreads : TickBounds<2>::kThreads);
+  if (storage == 0) return TickBounds<10>::kThreads;
+  switch (variant) {
+    case 0: return TickBounds<0>::kThreads;
+    case 1: return TickBounds<1>::kThreads;
+    case 2: return TickBounds<2>::kThreads;
+    default: return TickBounds<3>::kThreads;
+  }
 }
 
 cudaError_t launch_tick(int storage, int variant, const EngineArgs &ea, int grid, int block, cudaStream_t st) {
   if (block > tick_max_threads(storage, variant)) return cudaErrorInvalidConfiguration;
-  if (storage == 0) {
-    k_tick<StoreF64x18, 3><<<grid, block, 0, st>>>(ea);
-  } else if (variant == 0) {
-    k_tick<StoreF32x12, 0><<<grid, block, 0, st>>>(ea);
-  } else if (variant == 1) {
-    k_tick<StoreF32x12, 1><<<grid, block, 0, st>>>(ea);
-  } else {
-    k_tick<StoreF32x12, 2><<<grid, block, 0, st>>>(ea);
+  if (storage == 0) return tick_v<10>(ea, grid, block, st);
+  switch (variant) {
+    case 0: return tick_v<0>(ea, grid, block, st);
+    case 1: return tick_v<1>(ea, grid, block, st);
+    case 2: return tick_v<2>(ea, grid, block, st);
+    default: return tick_v<3>(ea, grid, block, st);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st) {
@@ -639,11 +677,13 @@ cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, doub
 cudaError_t tick_occupancy(int storage, int variant, int block, int *ctas_per_sm) {
   *ctas_per_sm = 0;
   if (block > tick_max_threads(storage, variant)) return cudaSuccess;
-  if (storage == 0)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF64x18, 3>, block, 0);
-  if (variant == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF32x12, 0>, block, 0);
-  if (variant == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF32x12, 1>, block, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_tick<StoreF32x12, 2>, block, 0);
+  if (storage == 0) return occ_v<10>(block, ctas_per_sm);
+  switch (variant) {
+    case 0: return occ_v<0>(block, ctas_per_sm);
+    case 1: return occ_v<1>(block, ctas_per_sm);
+    case 2: return occ_v<2>(block, ctas_per_sm);
+    default: return occ_v<3>(block, ctas_per_sm);
+  }
 }
 
 void host_advance_stage(const ChainDesc &d, ChainState &s) { advance_stage(d, s); }
