@@ -161,8 +161,8 @@ su3_status su3_lattice_info(su3_lattice *lat, size_t *links, size_t *bytes);
 
 /* Launch shape.  variant: register variant of the update kernel (FP32
  * storage: 0 = 128 registers / up to 256 threads, 1 = 96 / up to 128,
- * 2 = 96 / up to 128 and 3 = 128 / up to 256 with the loop over staple
- * directions kept rolled; FP64 storage: 0 only).  threads: CTA width, a multiple of 32 up to the
+ * 2 = 96 / up to 128, 3 = 128 / up to 256 and 4 = 85 / up to 256 with the
+ * loop over staple directions kept rolled; FP64 storage: 0 only).  threads: CTA width, a multiple of 32 up to the
  * variant's maximum.  ctas_per_sm = 0 launches one CTA per tile of `threads`
  * sites; > 0 a persistent grid of (SM count x ctas_per_sm) CTAs that loop
  * over the tiles.  The random numbers do not depend on the shape, so results

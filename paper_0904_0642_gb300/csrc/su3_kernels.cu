@@ -147,6 +147,8 @@ __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, 
   int offp, flp;
   step_fwd(d, sel(g.x, mu), mu, offp, flp);
   const int sp = g.s + offp, lp = layer ^ flp;  // x + mu
+  const uint2 key = make_uint2(d.seed_lo, d.seed_hi);
+  const uint32_t skey = site_key(d, g);
 
   M3<R> A = m3_zero<R>();
   if constexpr (ROLLED) {
@@ -161,8 +163,7 @@ __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, 
   typename S::Vec *pu = plane_ptr<S>(d, layer, colour, mu);
   M3<R> U = S::load(pu, Vh, jj);
   const R beta = sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d;
-  const uint2 key = make_uint2(d.seed_lo, d.seed_hi);
-  cm_update(U, A, beta, d.hits, key, site_key(d, g), sweep, colour, mu, nprop, nacc);
+  cm_update(U, A, beta, d.hits, key, skey, sweep, colour, mu, nprop, nacc);
   S::store(pu, Vh, jj, U);
 }
 
@@ -185,39 +186,66 @@ __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int j
 // in double: plaquettes split space/time, and Polyakov lines started at
 // x^D = 0 (the line follows the forward time neighbour until it closes).
 
+// (1/3) Re Tr(U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+) = (1/3) sum_ij
+// Re(P_ij conj(Q_ij)) with P = U_mu(x) U_nu(x+mu), Q = U_nu(x) U_mu(x+nu),
+// taken row by row so that few values are live at once.
+template <class S>
+__device__ __forceinline__ double plaquette_at(const ChainDesc &d, const SiteGeo &g, int colour, int mu, int nu,
+                                               int xmu, int xnu) {
+  using R = typename S::R;
+  const int Vh = d.Vh, layer = g.layer, jj = g.s >> 1, oc = colour ^ 1;
+  int offp, flp, offn, fln;
+  step_fwd(d, xmu, mu, offp, flp);
+  step_fwd(d, xnu, nu, offn, fln);
+  const M3<R> a = S::load(plane_ptr<S>(d, layer ^ flp, oc, nu), Vh, (g.s + offp) >> 1);  // U_nu(x+mu)
+  const M3<R> b = S::load(plane_ptr<S>(d, layer ^ fln, oc, mu), Vh, (g.s + offn) >> 1);  // U_mu(x+nu)
+  const M3<R> um = S::load(plane_ptr<S>(d, layer, colour, mu), Vh, jj);                  // U_mu(x)
+  const M3<R> un = S::load(plane_ptr<S>(d, layer, colour, nu), Vh, jj);                  // U_nu(x)
+  R tr = R(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    // row i of P and Q
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      C<R> p = cmul(um.e[i][0], a.e[0][j]);
+      cmac(p, um.e[i][1], a.e[1][j]);
+      cmac(p, um.e[i][2], a.e[2][j]);
+      C<R> q = cmul(un.e[i][0], b.e[0][j]);
+      cmac(q, un.e[i][1], b.e[1][j]);
+      cmac(q, un.e[i][2], b.e[2][j]);
+      tr = fm(p.re, q.re, tr);
+      tr = fm(p.im, q.im, tr);
+    }
+  }
+  return (double)tr * (1.0 / 3.0);
+}
+
+// Per thread: the two sites of checkerboard index jj (both colours).  Sums
+// in double: plaquettes split space/time, and Polyakov lines started at
+// x^D = 0 (the line follows the forward time neighbour until it closes).
 template <class S>
 __device__ __forceinline__ void measure_site(const ChainDesc &d, int layer, int jj, double acc[kPartVals]) {
   using R = typename S::R;
   const int Vh = d.Vh;
   const int D = d.D;
+#pragma unroll 1
   for (int colour = 0; colour < 2; ++colour) {
     const SiteGeo g = site_of(d, layer, colour, jj);
-    const int oc = colour ^ 1;
-#pragma unroll
-    for (int mu = 0; mu < kMaxD; ++mu) {
-      if (mu >= D) continue;
-      int offp, flp;
-      step_fwd(d, g.x[mu], mu, offp, flp);
-      const M3<R> umu = S::load(plane_ptr<S>(d, layer, colour, mu), Vh, jj);
-#pragma unroll
-      for (int nu = mu + 1; nu < kMaxD; ++nu) {
-        if (nu >= D) continue;
-        int offn, fln;
-        step_fwd(d, g.x[nu], nu, offn, fln);
-        const M3<R> a = S::load(plane_ptr<S>(d, layer ^ flp, oc, nu), Vh, (g.s + offp) >> 1);  // U_nu(x+mu)
-        const M3<R> b = S::load(plane_ptr<S>(d, layer ^ fln, oc, mu), Vh, (g.s + offn) >> 1);  // U_mu(x+nu)
-        const M3<R> c = S::load(plane_ptr<S>(d, layer, colour, nu), Vh, jj);                   // U_nu(x)
-        const M3<R> P = mul_nn(umu, a);
-        const M3<R> Q = mul_nn(c, b);
-        const double p = (double)retr_nd(P, Q) * (1.0 / 3.0);
+#pragma unroll 1
+    for (int mu = 0; mu < D; ++mu) {
+      const int xmu = sel(g.x, mu);
+#pragma unroll 1
+      for (int nu = mu + 1; nu < D; ++nu) {
+        const double p = plaquette_at<S>(d, g, colour, mu, nu, xmu, sel(g.x, nu));
         if (nu == D - 1) acc[1] += p; else acc[0] += p;
       }
     }
-    if (g.x[D - 1] == 0) {
+    const int t = D - 1;
+    if (sel(g.x, t) == 0) {
       // Polyakov line through (layer, x, x^D = 0)
-      const int t = D - 1;
       M3<R> P = S::load(plane_ptr<S>(d, layer, colour, t), Vh, jj);
       int cs = g.s, cl = layer, cc = colour, xt = 0;
+#pragma unroll 1
       for (int step = 0; step < 2 * d.dims[t]; ++step) {
         int off, fl;
         step_fwd(d, xt, t, off, fl);
@@ -351,13 +379,16 @@ __device__ __host__ inline void advance_stage(const ChainDesc &d, ChainState &s)
 // (Measured on the 32^4 workload: 80-register variants spill into L1 and lose
 // 4x; so do variants that prefetch the next staple direction into L1.)
 // kRolled: the update keeps its loop over staple directions rolled.
-// (Also measured and dropped: staging the staple links in shared memory with
-// cp.async - its 624 B per thread leave too few warps per SM.)
+// Measured on the 32^4 workload and dropped: staging the staple links in
+// shared memory with cp.async, and variants with 170 or more registers -
+// below 16 warps per SM the update falls off a latency cliff (3-4x slower);
+// computing the random numbers ahead of the staple adds spills.
 template <int V> struct TickBounds;
 template <> struct TickBounds<0> { static constexpr int kThreads = 256, kMinBlocks = 2; static constexpr bool kRolled = false; };   // FP32, 128 regs
 template <> struct TickBounds<1> { static constexpr int kThreads = 128, kMinBlocks = 5; static constexpr bool kRolled = false; };   // FP32, 96 regs
 template <> struct TickBounds<2> { static constexpr int kThreads = 128, kMinBlocks = 5; static constexpr bool kRolled = true; };    // FP32, rolled, 96 regs
 template <> struct TickBounds<3> { static constexpr int kThreads = 256, kMinBlocks = 2; static constexpr bool kRolled = true; };    // FP32, rolled, 128 regs
+template <> struct TickBounds<4> { static constexpr int kThreads = 256, kMinBlocks = 3; static constexpr bool kRolled = true; };    // FP32, rolled, 85 regs
 template <> struct TickBounds<10> { static constexpr int kThreads = 256, kMinBlocks = 1; static constexpr bool kRolled = false; };  // FP64
 
 template <class S, int V>
@@ -603,7 +634,7 @@ cudaError_t launch_measure_noalloc(int storage, const ChainDesc &d, int block, d
 
 // ------------------------------------------------------------------ launchers
 
-int tick_variants(int storage) { return storage == 0 ? 1 : 4; }
+int tick_variants(int storage) { return storage == 0 ? 1 : 5; }
 
 template <int V>
 static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_t st) {
@@ -628,7 +659,8 @@ int tick_max_threads(int storage, int variant) {
     case 0: return TickBounds<0>::kThreads;
     case 1: return TickBounds<1>::kThreads;
     case 2: return TickBounds<2>::kThreads;
-    default: return TickBounds<3>::kThreads;
+    case 3: return TickBounds<3>::kThreads;
+    default: return TickBounds<4>::kThreads;
   }
 }
 
@@ -639,7 +671,8 @@ cudaError_t launch_tick(int storage, int variant, const EngineArgs &ea, int grid
     case 0: return tick_v<0>(ea, grid, block, st);
     case 1: return tick_v<1>(ea, grid, block, st);
     case 2: return tick_v<2>(ea, grid, block, st);
-    default: return tick_v<3>(ea, grid, block, st);
+    case 3: return tick_v<3>(ea, grid, block, st);
+    default: return tick_v<4>(ea, grid, block, st);
   }
 }
 
@@ -682,7 +715,8 @@ cudaError_t tick_occupancy(int storage, int variant, int block, int *ctas_per_sm
     case 0: return occ_v<0>(block, ctas_per_sm);
     case 1: return occ_v<1>(block, ctas_per_sm);
     case 2: return occ_v<2>(block, ctas_per_sm);
-    default: return occ_v<3>(block, ctas_per_sm);
+    case 3: return occ_v<3>(block, ctas_per_sm);
+    default: return occ_v<4>(block, ctas_per_sm);
   }
 }
 

@@ -8,8 +8,8 @@ namespace su3g {
 
 // storage: 0 = FP64 18-real, 1 = FP32 12-real.
 // The tick kernel comes in variants (FP32: 0 = 128, 1 = 96 registers;
-// 2 = 96, 3 = 128 registers with a rolled staple loop; FP64: one); a variant
-// limits the CTA width to tick_max_threads.
+// 2 = 96, 3 = 128, 4 = 85 registers with a rolled staple loop; FP64: one);
+// a variant limits the CTA width to tick_max_threads.
 int tick_variants(int storage);
 int tick_max_threads(int storage, int variant);
 cudaError_t launch_tick(int storage, int variant, const EngineArgs &ea, int grid, int block, cudaStream_t st);

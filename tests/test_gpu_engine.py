@@ -65,7 +65,7 @@ def test_graph_and_launch_shape_do_not_change_links(storage):
     want = ref.get_links()
     shapes = [(0, 32, 1), (0, 64, 0), (0, 128, 2), (0, 256, 0)]
     if storage == su3.SU3_FP32_12:
-        shapes += [(1, 128, 0), (1, 96, 3), (1, 128, 1), (2, 64, 0), (2, 128, 0), (2, 256, 1)]
+        shapes += [(1, 128, 0), (1, 96, 3), (2, 64, 0), (2, 128, 1), (3, 256, 2), (4, 256, 0), (4, 128, 3)]
     for variant, threads, ctas in shapes:
         lat = su3.Lattice(dims, **kw)
         lat.set_launch(threads, ctas, variant=variant)
