@@ -350,25 +350,16 @@ def main():
 
     import paper_0904_0642_gb300 as su3
 
+    from paper_0904_0642_gb300.replicas import Replicas
+
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    reps = Replicas("nccl", device=torch.device("cuda", local))
+    barrier = reps.barrier
+    max_over_ranks = reps.max
 
     stream = torch.cuda.Stream()
-    lat = su3.Lattice(DIMS, beta=BETA, seed=SEED + rank, hits=HITS, storage=su3.SU3_FP32_12,
+    lat = su3.Lattice(DIMS, beta=BETA, seed=reps.seed(SEED), hits=HITS, storage=su3.SU3_FP32_12,
                       start=su3.SU3_START_HOT, reunit_every=SWEEPS_PER_STEP, measure_every=SWEEPS_PER_STEP,
                       measure_capacity=4096, stream=stream)
     if args.no_autotune:
@@ -482,8 +473,7 @@ def main():
     lat.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    reps.close()
 
 
 if __name__ == "__main__":
