@@ -65,9 +65,12 @@ def _configure(L):
     L.orc_link_heatbath.argtypes = [dp, dp, c_double, c_int, c_uint64, c_uint32, c_uint32, c_int, c_int,
                                     POINTER(c_uint64)]
     L.orc_link_chain.argtypes = [dp, dp, c_double, c_int, c_uint64, c_int64, dp]
-    L.orc_sweep.argtypes = [gp, dp, c_double, c_int, c_uint64, c_int64, c_int, POINTER(c_uint64), dp, dp]
-    L.orc_phase.argtypes = [gp, dp, c_double, c_int, c_uint64, c_int64, c_int, c_int, c_int64, c_int64,
+    L.orc_sweep.argtypes = [gp, dp, c_double, c_double, c_int, c_uint64, c_int64, c_int, POINTER(c_uint64), dp, dp]
+    L.orc_phase.argtypes = [gp, dp, c_double, c_double, c_int, c_uint64, c_int64, c_int, c_int, c_int64, c_int64,
                             POINTER(c_uint64), dp, dp]
+    L.orc_staple_weighted.argtypes = [gp, dp, c_int, c_int64, c_int, c_double, c_double, dp]
+    L.orc_action_weighted.argtypes = [gp, dp, c_double, c_double]
+    L.orc_action_weighted.restype = c_double
     L.orc_reunitarize.argtypes = [gp, dp]
     L.orc_reunitarize_matrix.argtypes = [dp]
     L.orc_plaquette.argtypes = [gp, dp, c_int, dp]
@@ -209,17 +212,19 @@ class Lattice:
         return self
 
     def sweep(self, beta: float, hits: int, seed: int, n: int = 1, sweep0: int | None = None, margins=None,
-              kmins=None):
+              kmins=None, beta1: float | None = None):
         """n checkerboard sweeps; returns [proposals, accepts].  margins and
         kmins, if given, are float64 arrays of nlinks entries (initialised to
         +inf) that receive per link the smallest accept-test margin and the
-        smallest SU(2) subgroup norm k seen."""
+        smallest SU(2) subgroup norm k seen.  beta1 (DLT only): coupling of
+        the plaquettes with a link in layer 1 (default: beta)."""
         if sweep0 is None:
             sweep0 = self.sweeps_done
         st = (c_uint64 * 2)()
         mp = _dp(margins) if margins is not None else None
         kp = _dp(kmins) if kmins is not None else None
-        lib().orc_sweep(self._g(), _dp(self.U), beta, hits, seed, sweep0, n, st, mp, kp)
+        lib().orc_sweep(self._g(), _dp(self.U), beta, beta if beta1 is None else beta1, hits, seed, sweep0, n, st,
+                        mp, kp)
         self.sweeps_done = sweep0 + n
         return int(st[0]), int(st[1])
 
@@ -228,7 +233,7 @@ class Lattice:
         """One (colour, direction) phase over sites [s_begin, s_end) of each
         layer; returns [proposals, accepts]."""
         st = (c_uint64 * 2)()
-        lib().orc_phase(self._g(), _dp(self.U), beta, hits, seed, sweep, colour, mu, s_begin,
+        lib().orc_phase(self._g(), _dp(self.U), beta, beta, hits, seed, sweep, colour, mu, s_begin,
                         self.V if s_end is None else s_end, st, None, None)
         return int(st[0]), int(st[1])
 
@@ -250,6 +255,16 @@ class Lattice:
         lib().orc_staple(self._g(), _dp(self.U), layer, site, mu, _dp(A))
         A = A.reshape(3, 3, 2)
         return A[..., 0] + 1j * A[..., 1]
+
+    def staple_weighted(self, layer: int, site: int, mu: int, beta0: float, beta1: float) -> np.ndarray:
+        A = np.zeros(18)
+        lib().orc_staple_weighted(self._g(), _dp(self.U), layer, site, mu, beta0, beta1, _dp(A))
+        A = A.reshape(3, 3, 2)
+        return A[..., 0] + 1j * A[..., 1]
+
+    def action_weighted(self, beta0: float, beta1: float) -> float:
+        """sum over plaquettes of beta_p (1/3) Re Tr U_p (Sec. 2.2 tagging)."""
+        return float(lib().orc_action_weighted(self._g(), _dp(self.U), beta0, beta1))
 
     def neighbour_table(self) -> np.ndarray:
         out = np.zeros((self.nlayers, self.V, self.D, 2), dtype=np.int64)

@@ -376,6 +376,50 @@ void orc_staple(const orc_geom *g, const double *U, int layer, int64_t s, int mu
   m_store(A18, &A);
 }
 
+/* DLT with two couplings (Sec. 2.2): every link carries the tag of its
+ * layer (0 or 1); a plaquette whose tag sum is zero has beta0, any other
+ * beta1.  The Wilson weight of a link is then exp((1/3) Re Tr(U A_w)) with
+ * the weighted staple A_w = sum over its plaquettes of beta_p times the
+ * staple of that plaquette.  Upper staple of nu: plaquette at x with links
+ * based at x, x+mu, x+nu, x; lower staple: plaquette at x-nu with links
+ * based at x-nu, x+mu-nu, x, x-nu. */
+static mat3 orc_staple_weighted_m(const orc_geom *g, const double *U, int layer, int64_t s, int mu, double beta0,
+                                  double beta1) {
+  mat3 A = m_zero();
+  int32_t lp; int64_t sp;
+  orc_neighbour(g, layer, s, mu, +1, &lp, &sp);
+  for (int nu = 0; nu < g->D; ++nu) {
+    if (nu == mu) continue;
+    int32_t ln; int64_t sn;
+    int32_t lm; int64_t sm;
+    int32_t lpm; int64_t spm;
+    orc_neighbour(g, layer, s, nu, +1, &ln, &sn);
+    orc_neighbour(g, layer, s, nu, -1, &lm, &sm);
+    orc_neighbour(g, lp, sp, nu, -1, &lpm, &spm);
+    double b_up = (layer + lp + ln + layer) ? beta1 : beta0;
+    double b_dn = (lm + lpm + layer + lm) ? beta1 : beta0;
+    mat3 a = link_at(g, U, lp, sp, nu);
+    mat3 b = link_at(g, U, ln, sn, mu); b = m_dag(&b);
+    mat3 c = link_at(g, U, layer, s, nu); c = m_dag(&c);
+    mat3 t = m_mul(&a, &b);
+    mat3 up = m_mul(&t, &c);
+    mat3 d = link_at(g, U, lpm, spm, nu); d = m_dag(&d);
+    mat3 e = link_at(g, U, lm, sm, mu); e = m_dag(&e);
+    mat3 f = link_at(g, U, lm, sm, nu);
+    mat3 t2 = m_mul(&d, &e);
+    mat3 dn = m_mul(&t2, &f);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) A.m[i][j] += b_up * up.m[i][j] + b_dn * dn.m[i][j];
+  }
+  return A;
+}
+
+void orc_staple_weighted(const orc_geom *g, const double *U, int layer, int64_t s, int mu, double beta0, double beta1,
+                         double *A18) {
+  mat3 A = orc_staple_weighted_m(g, U, layer, s, mu, beta0, beta1);
+  m_store(A18, &A);
+}
+
 /* ------------------------------------------------------------------ */
 /* SU(2) heatbath (Sec. 2.1: FHKP, multi-hit accept/reject).            */
 /* The paper cites the algorithm without formulas; this follows          */
@@ -547,20 +591,23 @@ void orc_link_chain(double *u18, const double *A18, double beta, int hits, uint6
 
 /* One (colour, direction) phase over the sites s_begin <= i_s - 1 < s_end
  * of every layer (the whole phase for [0, V)). */
-void orc_phase(const orc_geom *g, double *U, double beta, int hits, uint64_t seed, int64_t sweep, int colour, int mu,
-               int64_t s_begin, int64_t s_end, uint64_t *stats, double *margins, double *kmins) {
+void orc_phase(const orc_geom *g, double *U, double beta, double beta1, int hits, uint64_t seed, int64_t sweep,
+               int colour, int mu, int64_t s_begin, int64_t s_end, uint64_t *stats, double *margins, double *kmins) {
   int64_t V = orc_nsites(g);
   if (s_end > V) s_end = V;
+  const int weighted = g->nlayers == 2 && beta1 != beta; /* Sec. 2.2, two couplings */
   for (int l = 0; l < g->nlayers; ++l)
     for (int64_t s = s_begin; s < s_end; ++s) {
       int32_t x[ORC_MAXD];
       orc_site_coords(g, s, x);
       if (orc_colour(g, x) != colour) continue;
-      mat3 A = orc_staple_m(g, U, l, s, mu);
+      mat3 A = weighted ? orc_staple_weighted_m(g, U, l, s, mu, beta, beta1) : orc_staple_m(g, U, l, s, mu);
       double *p = (double *)link_ptr(g, U, l, s, mu);
       mat3 Ul = m_load(p);
       orc_link_stats st = {0, 0, INFINITY, INFINITY};
-      orc_cm_update(&Ul, &A, beta, hits, seed, orc_site_key(g, l, s), (uint32_t)sweep, colour, mu, &st);
+      /* with two couplings the staple already carries beta_p */
+      orc_cm_update(&Ul, &A, weighted ? 1.0 : beta, hits, seed, orc_site_key(g, l, s), (uint32_t)sweep, colour, mu,
+                    &st);
       m_store(p, &Ul);
       if (stats) { stats[0] += st.proposals; stats[1] += st.accepts; }
       int64_t idx = ((int64_t)l * V + s) * g->D + mu;
@@ -569,12 +616,13 @@ void orc_phase(const orc_geom *g, double *U, double beta, int hits, uint64_t see
     }
 }
 
-void orc_sweep(const orc_geom *g, double *U, double beta, int hits, uint64_t seed, int64_t sweep0, int nsweeps,
-               uint64_t *stats, double *margins, double *kmins) {
+void orc_sweep(const orc_geom *g, double *U, double beta, double beta1, int hits, uint64_t seed, int64_t sweep0,
+               int nsweeps, uint64_t *stats, double *margins, double *kmins) {
   int64_t V = orc_nsites(g);
   for (int64_t sw = sweep0; sw < sweep0 + nsweeps; ++sw)
     for (int colour = 0; colour < 2; ++colour)
-      for (int mu = 0; mu < g->D; ++mu) orc_phase(g, U, beta, hits, seed, sw, colour, mu, 0, V, stats, margins, kmins);
+      for (int mu = 0; mu < g->D; ++mu)
+        orc_phase(g, U, beta, beta1, hits, seed, sw, colour, mu, 0, V, stats, margins, kmins);
 }
 
 /* ------------------------------------------------------------------ */
@@ -618,6 +666,28 @@ void orc_plaquette(const orc_geom *g, const double *U, int layer, double out[3])
   out[0] = (sum_s + sum_t) / (double)(n_s + n_t);
   out[1] = n_s ? sum_s / (double)n_s : 0.0;
   out[2] = sum_t / (double)n_t;
+}
+
+/* sum over plaquettes of beta_p (1/3) Re Tr U_p, with beta_p from the tags
+ * (layers) of the plaquette's four links: beta1 if any is in layer 1 (Sec.
+ * 2.2).  Links of U_p = U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ are based at
+ * x, x+mu, x+nu and x. */
+double orc_action_weighted(const orc_geom *g, const double *U, double beta0, double beta1) {
+  int64_t V = orc_nsites(g);
+  double sum = 0;
+  for (int l = 0; l < g->nlayers; ++l)
+    for (int64_t s = 0; s < V; ++s)
+      for (int mu = 0; mu < g->D; ++mu)
+        for (int nu = mu + 1; nu < g->D; ++nu) {
+          int32_t lp, ln; int64_t sp, sn;
+          orc_neighbour(g, l, s, mu, +1, &lp, &sp);
+          orc_neighbour(g, l, s, nu, +1, &ln, &sn);
+          int tags[4] = {l, lp, ln, l};
+          int any = 0;
+          for (int k = 0; k < 4; ++k) any |= tags[k];
+          sum += (any ? beta1 : beta0) * orc_plaq_one(g, U, l, s, mu, nu);
+        }
+  return sum;
 }
 
 /* Polyakov loop (not in the paper): (1/3) Tr of the ordered product of

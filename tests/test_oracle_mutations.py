@@ -47,6 +47,10 @@ MUTATIONS = {
                              "a.m[1][k] = gauss[2 * k] + I * gauss[2 * k + 1] + 1e-9;"),
     "sweep_ignores_colour": ("if (orc_colour(g, x) != colour) continue;", ""),
     "polyakov_open_line": ("} while (!(cl == l && cs == s));", "} while (0);"),
+    "two_beta_tag_base_only": ("double b_up = (layer + lp + ln + layer) ? beta1 : beta0;",
+                               "double b_up = (layer) ? beta1 : beta0;"),
+    "two_beta_lower_tags": ("double b_dn = (lm + lpm + layer + lm) ? beta1 : beta0;",
+                            "double b_dn = (lm + layer) ? beta1 : beta0;"),
 }
 
 
@@ -160,8 +164,24 @@ def check_sweep():
     assert abs(m - exact.su3_plaquette_mean(1.0)) < 5 * err
 
 
+def check_two_beta():
+    rng = np.random.default_rng(5)
+    lat = oracle.Lattice([2, 4, 2, 4], nlayers=2, glue_mask=0b1111).hot_start(3)
+    for _ in range(6):
+        layer, site, mu = int(rng.integers(2)), int(rng.integers(lat.V)), int(rng.integers(4))
+        A = lat.staple_weighted(layer, site, mu, 5.0, 2.0)
+        s0 = lat.action_weighted(5.0, 2.0)
+        M = lat.links()
+        old = M[layer, site, mu].copy()
+        new = _random_su3(rng)
+        M[layer, site, mu] = new
+        lat.set_links(M)
+        s1 = lat.action_weighted(5.0, 2.0)
+        assert abs(3 * (s1 - s0) - np.real(np.trace((new - old) @ A))) < 1e-9
+
+
 CHECKS = [check_philox, check_dlt_neighbours, check_closed_form_configs, check_reunit_and_hot_start,
-          check_local_action_and_gauge, check_su2, check_sweep, check_frozen_staple]
+          check_local_action_and_gauge, check_su2, check_sweep, check_frozen_staple, check_two_beta]
 
 
 def test_unmutated_oracle_passes_quick_checks():
