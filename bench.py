@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -57,10 +58,16 @@ def measured_peaks():
 
 
 def kernel_hash():
+    """Hash of the kernel sources with comments and blank lines removed, so
+    that recorded ncu counters stay valid across comment edits."""
     h = hashlib.sha256()
     for f in ("su3_device.cuh", "su3_kernels.cu", "su3_engine.h"):
-        with open(os.path.join(ROOT, "paper_0904_0642_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_0904_0642_gb300", "csrc", f)) as fh:
+            src = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for ln in src.splitlines():
+            ln = ln.split("//", 1)[0].rstrip()
+            if ln:
+                h.update(ln.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
@@ -338,6 +345,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / FP64 / roofline passes")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape (for profiler runs)")
+    ap.add_argument("--variant", type=int, default=None, help="with --no-autotune: kernel variant")
+    ap.add_argument("--threads", type=int, default=128, help="with --no-autotune: CTA width")
+    ap.add_argument("--ctas", type=int, default=0, help="with --no-autotune: CTAs per SM (0: one per tile)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -363,7 +373,8 @@ def main():
                       start=su3.SU3_START_HOT, reunit_every=SWEEPS_PER_STEP, measure_every=SWEEPS_PER_STEP,
                       measure_capacity=4096, stream=stream)
     if args.no_autotune:
-        variant, threads, ctas, us = 0, 128, 0, None
+        variant, threads, ctas, us = (args.variant or 0), args.threads, args.ctas, None
+        lat.set_launch(threads, ctas, variant=variant)
     else:
         variant, threads, ctas, us = lat.autotune()
     links = lat.nlinks

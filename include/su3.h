@@ -78,12 +78,14 @@ typedef struct su3_config {
   void *stream;                 /* cudaStream_t, or NULL */
   void *link_buffer;            /* optional caller-owned device buffer for the links, or NULL */
   size_t link_buffer_bytes;     /* its size; must be >= su3_link_bytes() */
+  double beta1;                 /* DLT with two couplings (Sec. 2.2): beta of the plaquettes with a link in
+                                   layer 1; < 0 (the default of su3_config_init): equal to beta */
 } su3_config;
 
 typedef struct su3_lattice su3_lattice;
 
-/* Fill *cfg with defaults: D=4, 4^4, PBC, beta=6, seed=1, FP64_18, cold,
- * hits=2, no automatic re-unitarisation or measurement. */
+/* Fill *cfg with defaults: D=4, 4^4, PBC, beta=6 (beta1 = beta), seed=1,
+ * FP64_18, cold, hits=2, no automatic re-unitarisation or measurement. */
 void su3_config_init(su3_config *cfg);
 
 /* Device bytes the links of cfg need (0 if cfg is invalid). */
@@ -151,6 +153,19 @@ su3_status su3_set_links(su3_lattice *lat, const double *host, size_t n);
  * number of completed sweeps (the sweep counter of the random numbers). */
 su3_status su3_stats(su3_lattice *lat, uint64_t *proposals, uint64_t *accepts, uint64_t *sweeps);
 
+/* Action bookkeeping (Sec. 2.1: the update keeps track of the total action,
+ * checked now and then against a direct recalculation).  Every link update
+ * books its change of S = sum_p beta_p (1 - Re Tr U_p / 3): an accepted SU(2)
+ * subgroup changes Re Tr(U A) by 2 (k x0 - a0).  *booked = the action at the
+ * last reset + the booked changes since (summed in a fixed order); *direct =
+ * the action recomputed from the plaquette now (NaN for the two-coupling DLT;
+ * its *booked is then the change since the last reset).  Re-unitarisation
+ * and su3_set_links are not booked; su3_set_links resets.  Synchronises.
+ * su3_action_reset sets the reference to the direct action and clears the
+ * booked changes. */
+su3_status su3_action(su3_lattice *lat, double *booked, double *direct);
+su3_status su3_action_reset(su3_lattice *lat);
+
 /* Set the sweep counter (resume from a checkpoint taken with su3_get_links
  * and su3_stats: the counter-based random numbers make the continuation
  * bitwise identical). */
@@ -162,13 +177,14 @@ su3_status su3_lattice_info(su3_lattice *lat, size_t *links, size_t *bytes);
 /* Launch shape.  variant: register variant of the update kernel (FP32
  * storage: 0 = 128 registers / up to 256 threads, 1 = 96 / up to 128,
  * 2 = 96 / up to 128, 3 = 128 / up to 256 and 4 = 85 / up to 256 with the
- * loop over staple directions kept rolled; FP64 storage: 0 only).  threads: CTA width, a multiple of 32 up to the
- * variant's maximum.  ctas_per_sm = 0 launches one CTA per tile of `threads`
- * sites; > 0 a persistent grid of (SM count x ctas_per_sm) CTAs that loop
- * over the tiles.  The random numbers do not depend on the shape, so results
- * are identical for every choice.  su3_autotune times the candidates on this
- * lattice (on a scratch copy: links, counters and sweep counter are
- * restored) and keeps the fastest; outputs may be NULL. */
+ * loop over staple directions kept rolled; FP64 storage: 0 only).  threads:
+ * CTA width, a multiple of 32 up to the variant's maximum.  ctas_per_sm = 0
+ * launches one CTA per tile of `threads` sites; > 0 a persistent grid of
+ * (SM count x ctas_per_sm) CTAs that loop over the tiles.  The random
+ * numbers do not depend on the shape, so results are identical for every
+ * choice.  su3_autotune times the candidates on this lattice, each from the
+ * same links (links, counters and sweep counter are restored afterwards),
+ * and keeps the fastest; outputs may be NULL. */
 su3_status su3_set_launch(su3_lattice *lat, int variant, int threads, int ctas_per_sm);
 su3_status su3_autotune(su3_lattice *lat, int *variant, int *threads, int *ctas_per_sm, double *us_per_sweep);
 

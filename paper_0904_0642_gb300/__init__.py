@@ -34,7 +34,7 @@ SU3_START_COLD, SU3_START_HOT = 0, 1
 EXPORTED = [
     "su3_config_init", "su3_link_bytes", "su3_lattice_create", "su3_lattice_create_ex", "su3_lattice_destroy",
     "su3_sweep", "su3_reunitarize", "su3_plaquette", "su3_polyakov", "su3_measure_async", "su3_measurements",
-    "su3_get_links", "su3_set_links", "su3_stats", "su3_set_sweep_counter", "su3_lattice_info", "su3_set_launch",
+    "su3_get_links", "su3_set_links", "su3_stats", "su3_action", "su3_action_reset", "su3_set_sweep_counter", "su3_lattice_info", "su3_set_launch",
     "su3_autotune", "su3_use_graph", "su3_set_profiling", "su3_get_profile", "su3_ensemble_create", "su3_ensemble_destroy", "su3_ensemble_sweep",
     "su3_ensemble_measure", "su3_ensemble_get_links", "su3_ensemble_measurements", "su3_ensemble_set_launch", "su3_ensemble_autotune", "su3_ensemble_use_graph",
     "su3_ensemble_set_profiling", "su3_ensemble_get_profile",
@@ -55,7 +55,7 @@ class su3_config(Structure):
         ("beta", c_double), ("seed", c_uint64), ("storage", c_int32), ("start", c_int32), ("hits", c_int32),
         ("reunit_every", c_int32), ("measure_every", c_int32), ("measure_capacity", c_int32),
         ("layer_blind", c_int32), ("rng_period", c_int32 * MAX_D), ("stream", c_void_p), ("link_buffer", c_void_p),
-        ("link_buffer_bytes", c_size_t),
+        ("link_buffer_bytes", c_size_t), ("beta1", c_double),
     ]
 
 
@@ -107,6 +107,8 @@ def lib():
             "su3_set_links": (c_int, [vp, dp, sz]),
             "su3_stats": (c_int, [vp, u64p, u64p, u64p]),
             "su3_set_sweep_counter": (c_int, [vp, c_uint64]),
+            "su3_action": (c_int, [vp, dp, dp]),
+            "su3_action_reset": (c_int, [vp]),
             "su3_lattice_info": (c_int, [vp, POINTER(sz), POINTER(sz)]),
             "su3_set_launch": (c_int, [vp, c_int, c_int, c_int]),
             "su3_autotune": (c_int, [vp, POINTER(c_int), POINTER(c_int), POINTER(c_int), dp]),
@@ -237,6 +239,17 @@ def su3_stats(h):
     return p.value, a.value, s.value
 
 
+def su3_action(h):
+    """(booked, direct) action; see include/su3.h."""
+    b, d = c_double(), c_double()
+    _check(lib().su3_action(h, byref(b), byref(d)))
+    return b.value, d.value
+
+
+def su3_action_reset(h):
+    _check(lib().su3_action_reset(h))
+
+
 def su3_set_sweep_counter(h, sweeps: int):
     _check(lib().su3_set_sweep_counter(h, sweeps))
 
@@ -290,7 +303,7 @@ def su3_version() -> str:
 
 def make_config(dims, boundary=SU3_PBC, beta=6.0, seed=1, storage=SU3_FP64_18, start=SU3_START_COLD, hits=2,
                 glue_mask=0, reunit_every=0, measure_every=0, measure_capacity=0, layer_blind=False,
-                rng_period=None, stream=None, buffer=None) -> su3_config:
+                rng_period=None, stream=None, buffer=None, beta1=None) -> su3_config:
     c = su3_config_init()
     c.D = len(dims)
     for i, n in enumerate(dims):
@@ -306,6 +319,7 @@ def make_config(dims, boundary=SU3_PBC, beta=6.0, seed=1, storage=SU3_FP64_18, s
     c.measure_every = int(measure_every)
     c.measure_capacity = int(measure_capacity)
     c.layer_blind = int(bool(layer_blind))
+    c.beta1 = -1.0 if beta1 is None else float(beta1)
     if rng_period is not None:
         for i, p in enumerate(rng_period):
             c.rng_period[i] = int(p)
@@ -381,6 +395,12 @@ class Lattice:
 
     def set_sweep_counter(self, n):
         su3_set_sweep_counter(self.h, n)
+
+    def action(self):
+        return su3_action(self.h)
+
+    def action_reset(self):
+        su3_action_reset(self.h)
 
     def set_launch(self, threads, ctas_per_sm=0, variant=0):
         su3_set_launch(self.h, variant, threads, ctas_per_sm)

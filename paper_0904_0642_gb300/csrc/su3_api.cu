@@ -68,6 +68,7 @@ extern "C" void su3_config_init(su3_config *c) {
   c->storage = SU3_FP64_18;
   c->start = SU3_START_COLD;
   c->hits = 2;
+  c->beta1 = -1.0;
 }
 
 static su3_status validate(const su3_config *c) {
@@ -87,6 +88,7 @@ static su3_status validate(const su3_config *c) {
   if (V * layers * c->D * 9 >= 0x7fffffffLL)
     return fail(SU3_EINVAL, "lattice too large: link storage must stay below 2^31 16-byte vectors");
   if (!(c->beta >= 0.0) || !std::isfinite(c->beta)) return fail(SU3_EINVAL, "beta=%g must be finite and >= 0", c->beta);
+  if (!std::isfinite(c->beta1)) return fail(SU3_EINVAL, "beta1=%g must be finite (< 0: equal to beta)", c->beta1);
   if (c->hits < 1 || c->hits > 254) return fail(SU3_EINVAL, "hits=%d outside 1..254", c->hits);
   if (c->storage != SU3_FP64_18 && c->storage != SU3_FP32_12) return fail(SU3_EINVAL, "unknown storage %d", c->storage);
   if (c->start != SU3_START_COLD && c->start != SU3_START_HOT) return fail(SU3_EINVAL, "unknown start %d", c->start);
@@ -135,6 +137,9 @@ struct Chain {
   double *results = nullptr;
   double *partials = nullptr;
   unsigned long long *counters = nullptr;
+  double *action_slots = nullptr;  // booked action changes, one slot per warp of sites
+  int n_action_slots = 0;
+  double action_ref = 0.0;         // action at the last reset (su3_action)
   size_t link_bytes = 0;
   size_t bytes_total = 0;  // device bytes held (links if owned + scratch)
   uint64_t job_id = 0;     // server only
@@ -144,6 +149,7 @@ static void fill_desc(Chain &ch, int tile) {
   const su3_config &c = ch.cfg;
   ChainDesc &d = ch.desc;
   d.links = ch.links;
+  d.action_slots = ch.action_slots;
   d.results = ch.results;
   d.partials = ch.partials;
   d.counters = ch.counters;
@@ -191,10 +197,16 @@ static void fill_desc(Chain &ch, int tile) {
 
   d.beta_f = (float)c.beta;
   d.beta_d = c.beta;
+  const double b1 = c.beta1 >= 0.0 ? c.beta1 : c.beta;
+  d.weighted = (d.nlayers == 2 && b1 != c.beta) ? 1 : 0;
+  d.beta1_f = (float)b1;
+  d.beta1_d = b1;
+  d.action_factor = -(d.weighted ? 1.0 : c.beta) / 3.0;  // weighted: the staples carry the couplings
 }
 
 struct Engine {
   int storage = SU3_FP64_18;
+  bool weighted_any = false;  // some chain has two couplings: the tick kernel's weighted form
   cudaStream_t stream = nullptr;
   std::vector<Chain> chains;
   // device mirrors
@@ -246,7 +258,7 @@ struct Engine {
       CU(cudaEventCreate(&p.a));
       CU(cudaEventCreate(&p.b));
       CU(cudaEventRecord(p.a, stream));
-      CU(launch_tick(storage, variant, args(), grid, block, stream));
+      CU(launch_tick(storage, variant, weighted_any, args(), grid, block, stream));
       CU(cudaEventRecord(p.b, stream));
       prof_pending.push_back(p);
       if (s.active) {
@@ -308,6 +320,8 @@ struct Engine {
     cudaFree(ch.results);
     cudaFree(ch.partials);
     cudaFree(ch.counters);
+    cudaFree(ch.action_slots);
+    ch.action_slots = nullptr;
     ch.links = nullptr;
     ch.results = ch.partials = nullptr;
     ch.counters = nullptr;
@@ -356,6 +370,13 @@ struct Engine {
       return fail(SU3_ENOMEM, "scratch allocation failed");
     }
     ch.bytes_total += npart * sizeof(double) + nres * sizeof(double) + 16;
+    ch.n_action_slots = ch.desc.nlayers * ((ch.desc.Vh + 31) / 32);
+    if (cudaMalloc(&ch.action_slots, (size_t)ch.n_action_slots * sizeof(double)) != cudaSuccess) {
+      free_chain(ch);
+      return fail(SU3_ENOMEM, "action bookkeeping allocation failed");
+    }
+    CU(cudaMemsetAsync(ch.action_slots, 0, (size_t)ch.n_action_slots * sizeof(double), stream));
+    ch.bytes_total += (size_t)ch.n_action_slots * sizeof(double);
     CU(cudaMemsetAsync(ch.counters, 0, 2 * sizeof(unsigned long long), stream));
     CU(cudaMemsetAsync(ch.results, 0, nres * sizeof(double), stream));
     fill_desc(ch, block);
@@ -388,6 +409,12 @@ struct Engine {
     }
     total_tiles = tiles;
     if (ctas_per_sm <= 0 && tiles != old_tiles) drop_graph();  // the grid follows the tile count
+    bool w = false;
+    for (auto &ch : chains) w = w || ch.desc.weighted;
+    if (w != weighted_any) {  // another kernel form: the captured graph is stale
+      weighted_any = w;
+      drop_graph();
+    }
     if (chains.size() > chain_cap) {
       cudaFree(d_desc);
       cudaFree(d_state);
@@ -476,7 +503,7 @@ struct Engine {
   su3_status tick_direct(int n) {
     int grid = 0;
     TRY(grid_size(&grid));
-    for (int i = 0; i < n; ++i) CU(launch_tick(storage, variant, args(), grid, block, stream));
+    for (int i = 0; i < n; ++i) CU(launch_tick(storage, variant, weighted_any, args(), grid, block, stream));
     return SU3_OK;
   }
 
@@ -489,7 +516,7 @@ struct Engine {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kGraphTicks; ++i) {
-      cudaError_t e = launch_tick(storage, variant, args(), grid, block, stream);
+      cudaError_t e = launch_tick(storage, variant, weighted_any, args(), grid, block, stream);
       if (e != cudaSuccess) {
         cudaStreamEndCapture(stream, &g);
         if (g) cudaGraphDestroy(g);
@@ -596,6 +623,41 @@ struct Engine {
     CU(launch_convert(storage, d_desc + c, nlinks, canon, 0, stream));
     CU(cudaFreeAsync(canon, stream));
     CU(cudaStreamSynchronize(stream));
+    return action_reset(c);  // the links changed without bookkeeping
+  }
+
+  // Action S = sum_p beta (1 - Re Tr U_p / 3) from the plaquette (one coupling;
+  // NaN for the two-coupling DLT, whose per-plaquette betas it does not see).
+  su3_status direct_action(size_t c, double *S) {
+    Chain &ch = chains[c];
+    if (ch.desc.weighted) {
+      *S = std::nan("");
+      return SU3_OK;
+    }
+    double v[3 * kMeasVals];
+    TRY(measure_chain(c, v));
+    const double np = (double)ch.desc.nlayers * ch.desc.V * ch.desc.D * (ch.desc.D - 1) / 2;
+    *S = ch.cfg.beta * np * (1.0 - v[ch.desc.nlayers * kMeasVals]);
+    return SU3_OK;
+  }
+
+  su3_status booked_change(size_t c, double *dS) {
+    Chain &ch = chains[c];
+    if (!d_meas_out) CU(cudaMalloc(&d_meas_out, 3 * kMeasVals * sizeof(double)));
+    CU(launch_action_sum(ch.action_slots, ch.n_action_slots, d_meas_out, stream));
+    CU(cudaMemcpyAsync(h_pinned, d_meas_out, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CU(cudaStreamSynchronize(stream));
+    std::memcpy(dS, h_pinned, sizeof(double));
+    return SU3_OK;
+  }
+
+  su3_status action_reset(size_t c) {
+    Chain &ch = chains[c];
+    double S = 0.0;
+    TRY(direct_action(c, &S));
+    ch.action_ref = std::isnan(S) ? 0.0 : S;
+    CU(cudaMemsetAsync(ch.action_slots, 0, (size_t)ch.n_action_slots * sizeof(double), stream));
+    CU(cudaStreamSynchronize(stream));
     return SU3_OK;
   }
 
@@ -646,6 +708,7 @@ static su3_status make_lattice(const su3_config *cfg, su3_lattice **out) {
       st = lat->eng.start_chain(lat->eng.chains.back());
     }
     if (st == SU3_OK) st = lat->eng.rebuild();
+    if (st == SU3_OK) st = lat->eng.action_reset(0);
   }
   if (st != SU3_OK) {
     std::string msg = g_err;
@@ -785,6 +848,24 @@ extern "C" su3_status su3_stats(su3_lattice *lat, uint64_t *proposals, uint64_t 
   return SU3_OK;
 }
 
+extern "C" su3_status su3_action(su3_lattice *lat, double *booked, double *direct) {
+  LAT_CHECK(lat);
+  Engine &e = lat->eng;
+  if (e.tiles_dirty) TRY(e.rebuild());
+  double dS = 0.0, S = 0.0;
+  TRY(e.booked_change(0, &dS));
+  TRY(e.direct_action(0, &S));
+  if (booked) *booked = e.chains[0].action_ref + dS;
+  if (direct) *direct = S;
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_action_reset(su3_lattice *lat) {
+  LAT_CHECK(lat);
+  if (lat->eng.tiles_dirty) TRY(lat->eng.rebuild());
+  return lat->eng.action_reset(0);
+}
+
 extern "C" su3_status su3_set_sweep_counter(su3_lattice *lat, uint64_t sweeps) {
   LAT_CHECK(lat);
   if (sweeps > 0xffffffffull) return fail(SU3_EINVAL, "sweep counter is 32-bit");
@@ -863,10 +944,14 @@ static su3_status autotune_engine(Engine &e, int *variant, int *threads, int *ct
     for (int t : cand_t) {
       if (t > tick_max_threads(e.storage, v)) continue;
       int occ = 0;
-      if (tick_occupancy(e.storage, v, t, &occ) != cudaSuccess || occ < 1) continue;
+      if (tick_occupancy(e.storage, v, e.weighted_any, t, &occ) != cudaSuccess || occ < 1) continue;
       // 0 = one CTA per tile, then persistent grids of 1, 2, 4, ..., occ CTAs per SM
       for (int c = 0; c <= occ && st == SU3_OK; c = (c == 0) ? 1 : ((c < occ && 2 * c > occ) ? occ : 2 * c)) {
         if ((st = e.set_launch(v, t, c)) != SU3_OK) break;
+        // every candidate starts from the same links: without re-unitarisation
+        // FP32 links leave SU(3) within ~60 sweeps and the timings with them
+        for (size_t k = 0; k < e.chains.size(); ++k)
+          cudaMemcpyAsync(e.chains[k].links, backup[k], e.chains[k].link_bytes, cudaMemcpyDeviceToDevice, e.stream);
         e.use_graph = true;
         if ((st = e.sweep_all(1)) != SU3_OK) break;  // warm-up + graph capture
         cudaEventRecord(a, e.stream);
@@ -1072,7 +1157,7 @@ static size_t job_bytes(const su3_config &c) {
   const size_t layers = c.boundary == SU3_DLT ? 2 : 1;
   const size_t tiles = layers * ((V / 2 + 31) / 32);
   const size_t cap = c.measure_capacity > 0 ? (size_t)c.measure_capacity : 1024;
-  return link_bytes_of(&c) + tiles * kPartVals * 8 + cap * (layers + 1) * kMeasVals * 8 + 16;
+  return link_bytes_of(&c) + tiles * kPartVals * 8 + cap * (layers + 1) * kMeasVals * 8 + 16 + tiles * 8;
 }
 
 extern "C" su3_status su3_server_create(size_t hbm_budget_bytes, int max_slots, su3_server **out) {
@@ -1101,7 +1186,7 @@ extern "C" su3_status su3_server_create(size_t hbm_budget_bytes, int max_slots, 
     // persistent grid: its size does not depend on the resident jobs, so the
     // captured graph of ticks survives admissions and retirements
     int occ = 0;
-    if (tick_occupancy(SU3_FP32_12, srv->eng.variant, srv->eng.block, &occ) != cudaSuccess || occ < 1) occ = 1;
+    if (tick_occupancy(SU3_FP32_12, srv->eng.variant, false, srv->eng.block, &occ) != cudaSuccess || occ < 1) occ = 1;
     srv->eng.ctas_per_sm = occ;
   }
   srv->t0 = std::chrono::steady_clock::now();

@@ -210,22 +210,26 @@ __device__ __forceinline__ void acc_su3_2rows(M3<R> &A, const M3<R> &m) {
   }
 }
 
-// 1/sqrt(n) in double: a float seed refined by two Newton steps,
+// 1/sqrt(n) in double: a float seed refined by NEWTON Newton steps,
 // y <- y (3 - n y^2) / 2; each roughly squares the relative error
-// (~2e-7 -> ~1e-13 -> rounding level).
+// (~2e-7 -> ~1e-13 -> rounding level).  One step is ample for links stored
+// in FP32 (rounded to ~6e-8 afterwards), two reach double rounding.
+template <int NEWTON = 2>
 __device__ __forceinline__ double rsqrt_d(double n) {
   double y = (double)rsqrtf((float)n);
   const double h = 0.5 * n;
-  y = y * __fma_rn(-h * y, y, 1.5);
-  return y * __fma_rn(-h * y, y, 1.5);
+#pragma unroll
+  for (int k = 0; k < NEWTON; ++k) y = y * __fma_rn(-h * y, y, 1.5);
+  return y;
 }
 
 // Gram-Schmidt of rows 1, 2 in double, row 3 from the cross product.
+template <int NEWTON = 2>
 __device__ __forceinline__ void reunit_d(M3<double> &m) {
   double n1 = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) n1 += m.e[0][k].re * m.e[0][k].re + m.e[0][k].im * m.e[0][k].im;
-  double i1 = rsqrt_d(n1);
+  double i1 = rsqrt_d<NEWTON>(n1);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     m.e[0][k].re *= i1;
@@ -245,7 +249,7 @@ __device__ __forceinline__ void reunit_d(M3<double> &m) {
   double n2 = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) n2 += m.e[1][k].re * m.e[1][k].re + m.e[1][k].im * m.e[1][k].im;
-  double i2 = rsqrt_d(n2);
+  double i2 = rsqrt_d<NEWTON>(n2);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     m.e[1][k].re *= i2;
@@ -262,6 +266,27 @@ __device__ __forceinline__ M3<A> m3_cast(const M3<B> &b) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) a.e[i][j] = {A(b.e[i][j].re), A(b.e[i][j].im)};
   return a;
+}
+
+// A += w m for an SU(3) matrix m given by rows 0, 1 (row 2 from the cross
+// product), w a real weight (a plaquette's coupling).
+template <typename R>
+__device__ __forceinline__ void acc_su3_2rows_w(M3<R> &A, const M3<R> &m, R w) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      A.e[i][j].re = fm(w, m.e[i][j].re, A.e[i][j].re);
+      A.e[i][j].im = fm(w, m.e[i][j].im, A.e[i][j].im);
+    }
+  const C<R> *a = m.e[0], *b = m.e[1];
+  const C<R> r2[3] = {conj_cross(a[1], b[2], a[2], b[1]), conj_cross(a[2], b[0], a[0], b[2]),
+                      conj_cross(a[0], b[1], a[1], b[0])};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    A.e[2][j].re = fm(w, r2[j].re, A.e[2][j].re);
+    A.e[2][j].im = fm(w, r2[j].im, A.e[2][j].im);
+  }
 }
 
 // ------------------------------------------------------------------ storage
@@ -469,10 +494,15 @@ __device__ __forceinline__ void rotate_rows(M3<R> &m, int i, int j, R r0, R r1, 
   }
 }
 
+// dretr (out): the change of Re Tr(U A) = Re Tr W.  An accepted subgroup
+// replaces Re(w_ii + w_jj) = 2 a0 = 2 k v0 by 2 k x0 and leaves the third
+// diagonal element alone, so the change is the sum of 2 (k x0 - a0).
 template <typename R>
 __device__ __forceinline__ void cm_update(M3<R> &U, const M3<R> &A, R beta, int hits, uint2 key, uint32_t c0,
-                                          uint32_t c1, int colour, int mu, uint32_t &nprop, uint32_t &nacc) {
+                                          uint32_t c1, int colour, int mu, uint32_t &nprop, uint32_t &nacc,
+                                          R &dretr) {
   M3<R> W = mul_nn(U, A);
+  dretr = R(0);
 #pragma unroll
   for (int sg = 0; sg < 3; ++sg) {
     const int i = (sg == 2) ? 1 : 0;
@@ -487,6 +517,7 @@ __device__ __forceinline__ void cm_update(M3<R> &U, const M3<R> &A, R beta, int 
     R x[4];
     if (!su2_draw(alpha, hits, key, c0, c1, heatbath_tag(colour, mu, sg), x, nprop)) continue;
     ++nacc;
+    dretr += R(2) * (k * x[0] - a0);
     const R ik = R(1) / k;
     const R v0 = a0 * ik, v1 = a1 * ik, v2 = a2 * ik, v3 = a3 * ik;
     // r = x v^+ as quaternions: r0 = x0 v0 + x.v, r = -x0 v + v0 x + x cross v

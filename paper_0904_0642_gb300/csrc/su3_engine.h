@@ -39,6 +39,7 @@ struct ChainDesc {
   double *results;           // [result_cap][nlayers + 1][kMeasVals]
   double *partials;          // [tiles][kPartVals]
   unsigned long long *counters;  // [proposals, accepts]
+  double *action_slots;      // booked action changes, one slot per warp of sites: [layer][ceil(Vh/32)]
   uint32_t seed_lo, seed_hi;
   int32_t D, nlayers, glue_mask, layer_blind;
   int32_t custom_period;     // 0: site key = layer*V + i_s - 1
@@ -57,6 +58,13 @@ struct ChainDesc {
   int32_t shift[kMaxD];      // log2 n^i when pow2
   float beta_f;
   double beta_d;
+  // DLT with two couplings (Sec. 2.2): weighted = 1 when beta1 != beta; a
+  // plaquette with any link in layer 1 then has beta1, and the staple is
+  // accumulated with these weights (the heatbath runs with beta = 1).
+  int32_t weighted;
+  float beta1_f;
+  double beta1_d;
+  double action_factor;      // booked dS per unit change of Re Tr(U A): -beta/3, or -1/3 when weighted
 };
 
 struct ChainState {

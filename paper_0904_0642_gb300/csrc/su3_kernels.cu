@@ -108,7 +108,7 @@ __device__ __forceinline__ int sel(const int (&x)[kMaxD], int i) {
 // ------------------------------------------------------------------ one link update
 
 // The staples of one direction nu added to A.
-template <class S>
+template <class S, bool WT>
 __device__ __forceinline__ void add_staples(const ChainDesc &d, const SiteGeo &g, int colour, int mu, int nu, int xnu,
                                             int sp, int lp, M3<typename S::R> &A) {
   using R = typename S::R;
@@ -126,21 +126,33 @@ __device__ __forceinline__ void add_staples(const ChainDesc &d, const SiteGeo &g
   M3<R> cb = mul_nn_2(c, b);
   third_row(cb);
   const M3<R> a = S::load2(plane_ptr<S>(d, lp, oc, nu), Vh, sp >> 1);      // U_nu(x+mu)
-  acc_su3_2rows(A, mul_nd_2(a, cb));
+  // WT (a kernel compiled for two-coupling chains) and a two-coupling chain:
+  // each staple enters with the coupling of its plaquette, beta1 when any of
+  // its links lies in layer 1, so A carries the betas and the heatbath runs
+  // with beta = 1.  Otherwise plain sums (beta enters the heatbath).
+  const bool weighted = WT && d.weighted;
+  const R b0 = sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d, b1 = sizeof(R) == 4 ? (R)d.beta1_f : (R)d.beta1_d;
+  if (weighted)
+    acc_su3_2rows_w(A, mul_nd_2(a, cb), (layer | lp | ln) ? b1 : b0);
+  else
+    acc_su3_2rows(A, mul_nd_2(a, cb));
   // lower staple U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) = (e f)^+ h
   const M3<R> f = S::load(plane_ptr<S>(d, lpm, colour, nu), Vh, spm >> 1); // U_nu(x+mu-nu)
   const M3<R> e = S::load2(plane_ptr<S>(d, lm, oc, mu), Vh, sm >> 1);      // U_mu(x-nu)
   M3<R> ef = mul_nn_2(e, f);
   third_row(ef);
   const M3<R> h = S::load(plane_ptr<S>(d, lm, oc, nu), Vh, sm >> 1);       // U_nu(x-nu)
-  acc_su3_2rows(A, mul_dn_2(ef, h));
+  if (weighted)
+    acc_su3_2rows_w(A, mul_dn_2(ef, h), (lm | lpm | layer) ? b1 : b0);
+  else
+    acc_su3_2rows(A, mul_dn_2(ef, h));
 }
 
 // ROLLED: the loop over staple directions stays a loop (no unrolling), so the
 // compiler cannot hoist later directions' loads; fewer registers, less code.
-template <class S, bool ROLLED>
+template <class S, bool ROLLED, bool WT>
 __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, int colour, int mu, int layer, int jj,
-                                            uint32_t &nprop, uint32_t &nacc) {
+                                            uint32_t &nprop, uint32_t &nacc, typename S::R &dretr) {
   using R = typename S::R;
   const int Vh = d.Vh;
   const SiteGeo g = site_of(d, layer, colour, jj);
@@ -154,18 +166,19 @@ __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, 
   if constexpr (ROLLED) {
 #pragma unroll 1
     for (int nu = 0; nu < d.D; ++nu)
-      if (nu != mu) add_staples<S>(d, g, colour, mu, nu, sel(g.x, nu), sp, lp, A);
+      if (nu != mu) add_staples<S, WT>(d, g, colour, mu, nu, sel(g.x, nu), sp, lp, A);
   } else {
 #pragma unroll
     for (int nu = 0; nu < kMaxD; ++nu)
-      if (nu < d.D && nu != mu) add_staples<S>(d, g, colour, mu, nu, g.x[nu], sp, lp, A);
+      if (nu < d.D && nu != mu) add_staples<S, WT>(d, g, colour, mu, nu, g.x[nu], sp, lp, A);
   }
   typename S::Vec *pu = plane_ptr<S>(d, layer, colour, mu);
   M3<R> U = S::load(pu, Vh, jj);
-  const R beta = sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d;
-  cm_update(U, A, beta, d.hits, key, skey, sweep, colour, mu, nprop, nacc);
+  const R beta = (WT && d.weighted) ? R(1) : (sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d);
+  cm_update(U, A, beta, d.hits, key, skey, sweep, colour, mu, nprop, nacc, dretr);
   S::store(pu, Vh, jj, U);
 }
+
 
 // ------------------------------------------------------------------ re-unitarisation
 
@@ -176,7 +189,7 @@ __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int j
     for (int mu = 0; mu < d.D; ++mu) {
       typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
       M3<double> m = m3_cast<double>(S::load(p, Vh, jj));
-      reunit_d(m);
+      reunit_d<sizeof(typename S::R) == 4 ? 1 : 2>(m);
       S::store(p, Vh, jj, m3_cast<typename S::R>(m));
     }
 }
@@ -376,13 +389,13 @@ __device__ __host__ inline void advance_stage(const ChainDesc &d, ChainState &s)
 
 // Register variants of the tick kernel: __launch_bounds__(threads, CTAs per
 // SM) caps registers at 65536 / (threads x CTAs).  The autotuner times them.
-// (Measured on the 32^4 workload: 80-register variants spill into L1 and lose
-// 4x; so do variants that prefetch the next staple direction into L1.)
 // kRolled: the update keeps its loop over staple directions rolled.
-// Measured on the 32^4 workload and dropped: staging the staple links in
-// shared memory with cp.async, and variants with 170 or more registers -
-// below 16 warps per SM the update falls off a latency cliff (3-4x slower);
-// computing the random numbers ahead of the staple adds spills.
+// On the 32^4 workload (one update phase, fresh re-unitarised lattice per
+// shape) the best shapes are within 5 % of each other: 128 registers at
+// 16 warps per SM is fastest; 96 and 85 registers (spills) are 3-10 % and
+// the unconstrained 156 registers (12 warps) 14 % slower.  Dropped after
+// measuring: a split into a staple kernel and a heatbath kernel (30 %
+// slower), an L1 prefetch of the next staple direction's links (8 %).
 template <int V> struct TickBounds;
 template <> struct TickBounds<0> { static constexpr int kThreads = 256, kMinBlocks = 2; static constexpr bool kRolled = false; };   // FP32, 128 regs
 template <> struct TickBounds<1> { static constexpr int kThreads = 128, kMinBlocks = 5; static constexpr bool kRolled = false; };   // FP32, 96 regs
@@ -391,7 +404,9 @@ template <> struct TickBounds<3> { static constexpr int kThreads = 256, kMinBloc
 template <> struct TickBounds<4> { static constexpr int kThreads = 256, kMinBlocks = 3; static constexpr bool kRolled = true; };    // FP32, rolled, 85 regs
 template <> struct TickBounds<10> { static constexpr int kThreads = 256, kMinBlocks = 1; static constexpr bool kRolled = false; };  // FP64
 
-template <class S, int V>
+// WT: compiled for engines holding a two-coupling DLT chain (any chain with
+// beta1 != beta); unweighted chains compute identically in both forms.
+template <class S, int V, bool WT>
 __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBlocks) k_tick(EngineArgs ea) {
   __shared__ ChainDesc sd;
   __shared__ ChainState ss;
@@ -399,6 +414,7 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
   const int total = ea.hdr->total_tiles;
   int cur = -1;
   uint32_t np = 0, na = 0;  // FHKP counters of the current chain, flushed per warp
+  bool wrote_partials = false;  // this thread wrote data that the last warp reads
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     const int c = __ldg(ea.tile_chain + t);  // the same for every thread of the CTA
     if (c != cur) {
@@ -415,25 +431,38 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
     const bool valid = jj < sd.Vh;
     if (ss.stage < 2 * sd.D) {
       const int colour = ss.stage / sd.D, mu = ss.stage - colour * sd.D;
-      if (valid) update_site<S, TickBounds<V>::kRolled>(sd, ss.sweep, colour, mu, layer, jj, np, na);
+      typename S::R dr = 0;  // change of Re Tr(U A), in the kernel's precision
+      if (valid) update_site<S, TickBounds<V>::kRolled, WT>(sd, ss.sweep, colour, mu, layer, jj, np, na, dr);
+      // book the action change S = sum_p beta_p (1 - Re Tr U_p / 3): each warp
+      // owns the slot of its 32 sites, so the one fire-and-forget add per warp
+      // meets no other add in this launch and the order of adds is fixed
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dr += __shfl_down_sync(0xffffffffu, dr, o);
+      if ((threadIdx.x & 31) == 0 && sd.action_slots)
+        atomicAdd(sd.action_slots + layer * ((sd.Vh + 31) >> 5) + (jj >> 5), sd.action_factor * (double)dr);
     } else if (ss.stage == kStageReunit) {
       if (valid) reunit_site<S>(sd, layer, jj);
     } else {
       double v[kPartVals] = {0, 0, 0, 0};
       if (valid) measure_site<S>(sd, layer, jj, v);
       block_reduce(v, s_red);
-      if (threadIdx.x == 0)
+      if (threadIdx.x == 0) {
         for (int k = 0; k < kPartVals; ++k) sd.partials[(size_t)lt * kPartVals + k] = v[k];
+        wrote_partials = true;
+      }
     }
   }
   if (cur >= 0) flush_counters(sd, np, na);
   // The last warp of the grid to finish advances the stage machines and
   // finishes measurements.  Counting warps, not CTAs, lets a warp leave as
-  // soon as its own work is done (no CTA-wide barrier at the end).
+  // soon as its own work is done (no CTA-wide barrier at the end).  Only the
+  // measurement partials are read by the last warp, so only their writers
+  // fence before counting (release); link stores and counter adds are
+  // ordered for the next launch by the launch boundary.
   const int lane = threadIdx.x & 31;
   unsigned prev = 0;
   if (lane == 0) {
-    __threadfence();
+    if (wrote_partials) __threadfence();
     prev = atomicAdd(&ea.hdr->done_warps, 1u);
   }
   prev = __shfl_sync(0xffffffffu, prev, 0);
@@ -481,6 +510,20 @@ __global__ void __launch_bounds__(256) k_measure(ChainDesc *desc_dev) {
 __global__ void k_measure_finalize(ChainDesc *desc_dev, double *out) {
   const ChainDesc d = *desc_dev;
   finalize_measure(d, d.partials, out);
+}
+
+// Sum of a chain's booked action changes, one warp, fixed order.
+__global__ void k_action_sum(const double *slots, int n, double *out) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) v += slots[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (threadIdx.x == 0) *out = v;
+}
+
+cudaError_t launch_action_sum(const double *slots, int n, double *out, cudaStream_t st) {
+  k_action_sum<<<1, 32, 0, st>>>(slots, n, out);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ start configurations
@@ -636,21 +679,21 @@ cudaError_t launch_measure_noalloc(int storage, const ChainDesc &d, int block, d
 
 int tick_variants(int storage) { return storage == 0 ? 1 : 5; }
 
-template <int V>
+template <int V, bool WT>
 static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_t st) {
   if constexpr (V == 10)
-    k_tick<StoreF64x18, 10><<<grid, block, 0, st>>>(ea);
+    k_tick<StoreF64x18, 10, WT><<<grid, block, 0, st>>>(ea);
   else
-    k_tick<StoreF32x12, V><<<grid, block, 0, st>>>(ea);
+    k_tick<StoreF32x12, V, WT><<<grid, block, 0, st>>>(ea);
   return cudaGetLastError();
 }
 
-template <int V>
+template <int V, bool WT>
 static cudaError_t occ_v(int block, int *ctas) {
   if constexpr (V == 10)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF64x18, 10>, block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF64x18, 10, WT>, block, 0);
   else
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF32x12, V>, block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF32x12, V, WT>, block, 0);
 }
 
 int tick_max_threads(int storage, int variant) {
@@ -664,16 +707,24 @@ int tick_max_threads(int storage, int variant) {
   }
 }
 
-cudaError_t launch_tick(int storage, int variant, const EngineArgs &ea, int grid, int block, cudaStream_t st) {
-  if (block > tick_max_threads(storage, variant)) return cudaErrorInvalidConfiguration;
-  if (storage == 0) return tick_v<10>(ea, grid, block, st);
+template <bool WT>
+static cudaError_t launch_tick_w(int storage, int variant, const EngineArgs &ea, int grid, int block,
+                                 cudaStream_t st) {
+  if (storage == 0) return tick_v<10, WT>(ea, grid, block, st);
   switch (variant) {
-    case 0: return tick_v<0>(ea, grid, block, st);
-    case 1: return tick_v<1>(ea, grid, block, st);
-    case 2: return tick_v<2>(ea, grid, block, st);
-    case 3: return tick_v<3>(ea, grid, block, st);
-    default: return tick_v<4>(ea, grid, block, st);
+    case 0: return tick_v<0, WT>(ea, grid, block, st);
+    case 1: return tick_v<1, WT>(ea, grid, block, st);
+    case 2: return tick_v<2, WT>(ea, grid, block, st);
+    case 3: return tick_v<3, WT>(ea, grid, block, st);
+    default: return tick_v<4, WT>(ea, grid, block, st);
   }
+}
+
+cudaError_t launch_tick(int storage, int variant, bool weighted, const EngineArgs &ea, int grid, int block,
+                        cudaStream_t st) {
+  if (block > tick_max_threads(storage, variant)) return cudaErrorInvalidConfiguration;
+  return weighted ? launch_tick_w<true>(storage, variant, ea, grid, block, st)
+                  : launch_tick_w<false>(storage, variant, ea, grid, block, st);
 }
 
 cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st) {
@@ -707,17 +758,23 @@ cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, doub
   return cudaGetLastError();
 }
 
-cudaError_t tick_occupancy(int storage, int variant, int block, int *ctas_per_sm) {
+template <bool WT>
+static cudaError_t tick_occupancy_w(int storage, int variant, int block, int *ctas_per_sm) {
+  if (storage == 0) return occ_v<10, WT>(block, ctas_per_sm);
+  switch (variant) {
+    case 0: return occ_v<0, WT>(block, ctas_per_sm);
+    case 1: return occ_v<1, WT>(block, ctas_per_sm);
+    case 2: return occ_v<2, WT>(block, ctas_per_sm);
+    case 3: return occ_v<3, WT>(block, ctas_per_sm);
+    default: return occ_v<4, WT>(block, ctas_per_sm);
+  }
+}
+
+cudaError_t tick_occupancy(int storage, int variant, bool weighted, int block, int *ctas_per_sm) {
   *ctas_per_sm = 0;
   if (block > tick_max_threads(storage, variant)) return cudaSuccess;
-  if (storage == 0) return occ_v<10>(block, ctas_per_sm);
-  switch (variant) {
-    case 0: return occ_v<0>(block, ctas_per_sm);
-    case 1: return occ_v<1>(block, ctas_per_sm);
-    case 2: return occ_v<2>(block, ctas_per_sm);
-    case 3: return occ_v<3>(block, ctas_per_sm);
-    default: return occ_v<4>(block, ctas_per_sm);
-  }
+  return weighted ? tick_occupancy_w<true>(storage, variant, block, ctas_per_sm)
+                  : tick_occupancy_w<false>(storage, variant, block, ctas_per_sm);
 }
 
 void host_advance_stage(const ChainDesc &d, ChainState &s) { advance_stage(d, s); }

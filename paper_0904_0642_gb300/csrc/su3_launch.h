@@ -9,16 +9,21 @@ namespace su3g {
 // storage: 0 = FP64 18-real, 1 = FP32 12-real.
 // The tick kernel comes in variants (FP32: 0 = 128, 1 = 96 registers;
 // 2 = 96, 3 = 128, 4 = 85 registers with a rolled staple loop; FP64: one);
-// a variant limits the CTA width to tick_max_threads.
+// a variant limits the CTA width to tick_max_threads.  weighted selects the
+// form compiled for two-coupling DLT chains (needed when any chain of the
+// launch has beta1 != beta).
 int tick_variants(int storage);
 int tick_max_threads(int storage, int variant);
-cudaError_t launch_tick(int storage, int variant, const EngineArgs &ea, int grid, int block, cudaStream_t st);
+cudaError_t launch_tick(int storage, int variant, bool weighted, const EngineArgs &ea, int grid, int block,
+                        cudaStream_t st);
 cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st);
 cudaError_t launch_start(int storage, ChainDesc *desc_dev, size_t nlinks, int hot, cudaStream_t st);
 cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, double *canon, int to_canonical,
                            cudaStream_t st);
-cudaError_t tick_occupancy(int storage, int variant, int block, int *ctas_per_sm);
+cudaError_t tick_occupancy(int storage, int variant, bool weighted, int block, int *ctas_per_sm);
 void host_advance_stage(const ChainDesc &d, ChainState &s);
+// Fixed-order sum of n booked action-change slots into *out (device).
+cudaError_t launch_action_sum(const double *slots, int n, double *out, cudaStream_t st);
 // Measurement with partial sums in the library's static device scratch
 // (su3_measure_noalloc); the descriptor is passed by value.
 int noalloc_max_tiles();

@@ -183,3 +183,23 @@ def test_acceptance_counters():
     assert sweeps == 20
     assert prop == 20 * 3 * lat.nlinks  # one proposal per subgroup per link at hits = 1
     assert 0.95 < acc / prop < 0.995    # about 97 per cent in the scaling region (Sec. 2.1)
+
+
+def test_two_coupling_chain_in_ensemble_leaves_others_bitwise():
+    """A two-coupling DLT chain switches the fused launch to the tick
+    kernel's weighted form; the other chains (and the weighted chain itself)
+    must still equal their runs alone, bit for bit."""
+    cfgs = [su3.make_config([4, 4, 4, 4], boundary=su3.SU3_DLT, beta=6.0, beta1=4.5, seed=31,
+                            storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT, hits=2),
+            su3.make_config([8, 8, 8, 8], beta=5.9, seed=32, storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT,
+                            hits=2),
+            su3.make_config([6, 6, 6, 4], boundary=su3.SU3_DLT, beta=5.7, seed=33, storage=su3.SU3_FP32_12,
+                            start=su3.SU3_START_HOT, hits=1)]
+    ens = su3.Ensemble(cfgs)
+    ens.sweep(4)
+    for i, cfg in enumerate(cfgs):
+        dims = [cfg.dims[k] for k in range(cfg.D)]
+        alone = su3.Lattice(dims, boundary=cfg.boundary, beta=cfg.beta, beta1=(cfg.beta1 if cfg.beta1 >= 0 else None),
+                            seed=cfg.seed, storage=cfg.storage, start=cfg.start, hits=cfg.hits)
+        alone.sweep(4)
+        assert np.array_equal(ens.get_links(i), alone.get_links()), i

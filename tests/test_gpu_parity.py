@@ -4,8 +4,10 @@ link, through the C ABI.
 Tolerances: FP64 storage <= 1e-11 per link element after one sweep; FP32
 12-real storage <= 1e-5, where a link outside it is counted (and must be
 explained by the oracle): an accept/reject decision within the float
-rounding of its threshold, or an SU(2) subgroup with a small norm k, whose
-direction a/k amplifies the float rounding of W = U A by 1/k.
+rounding of its threshold, or an ill-conditioned update - one whose oracle
+result moves by much under a rounding-level perturbation of the start (a
+subgroup with a small norm k, whose direction a/k amplifies the float
+rounding of W = U A).
 """
 import numpy as np
 import pytest
@@ -70,22 +72,35 @@ def test_set_get_round_trip(storage, tol):
         assert np.max(np.abs(lat.get_links() - o.U)) <= tol
 
 
-def _flip_check(got, want, margins, kmins, tol):
+def _sensitivity(make, start, **sweep_kw):
+    """Each link's response, in the oracle, to a perturbation of the start at
+    float rounding level (every element times 1 + 2^-24 r, r uniform in
+    [-1, 1]): the empirical condition of the one-sweep update."""
+    rng = np.random.default_rng(99)
+    a, b = make(), make()
+    a.U[...] = start
+    b.U[...] = start * (1 + 2.0 ** -24 * rng.uniform(-1, 1, start.shape))
+    a.sweep(**sweep_kw)
+    b.sweep(**sweep_kw)
+    return np.max(np.abs(a.U - b.U).reshape(-1, 18), axis=1)
+
+
+def _flip_check(got, want, margins, sens, tol):
     """Links beyond tol are counted, not failed, when the oracle explains
     them: an accept/reject decision within FLIP_MARGIN of its threshold (a
-    flip), or an ill-conditioned subgroup, whose direction v = a/k carries
-    the float rounding of W (~1e-6) amplified by 1/k; such a link must still
-    be within 4e-6/k_min.  Returns the number of counted links."""
+    flip), or a link whose own response to rounding-level perturbations of
+    the start is large (an ill-conditioned update, e.g. a subgroup with small
+    k, whose direction a/k amplifies the rounding of W); such a link must
+    stay within 30 times that response.  Returns the number counted."""
     err = np.max(np.abs(got - want).reshape(-1, 18), axis=1)
     margins = margins.reshape(-1)
-    kmins = kmins.reshape(-1)
     over = err > tol
     flip = margins < FLIP_MARGIN
-    conditioned = err <= np.maximum(tol, 4e-6 / kmins)
+    conditioned = err <= np.maximum(tol, 30.0 * sens)
     unexplained = over & ~flip & ~conditioned
     assert not unexplained.any(), (
         f"{int(unexplained.sum())} links differ beyond the FP32 bound: err={err[unexplained][:5]}, "
-        f"margin={margins[unexplained][:5]}, kmin={kmins[unexplained][:5]}")
+        f"margin={margins[unexplained][:5]}, sensitivity={sens[unexplained][:5]}")
     return int(over.sum())
 
 
@@ -112,13 +127,13 @@ def test_one_sweep_fp32(g):
         start = lat.get_links()  # the float-rounded start both sides use
     o.U[...] = start
     margins = np.full(o.nlinks, np.inf)
-    kmins = np.full(o.nlinks, np.inf)
-    o.sweep(6.0, 2, 7, n=1, margins=margins, kmins=kmins)
+    o.sweep(6.0, 2, 7, n=1, margins=margins)
+    sens = _sensitivity(lambda: oracle_lattice(g), start, beta=6.0, hits=2, seed=7, n=1)
     with gpu_lattice(g, su3.SU3_FP32_12, beta=6.0, seed=7, hits=2) as lat:
         lat.set_links(start)
         lat.sweep(1)
         got = lat.get_links()
-    counted = _flip_check(got, o.U, margins, kmins, FP32_TOL)
+    counted = _flip_check(got, o.U, margins, sens, FP32_TOL)
     assert counted <= max(2, o.nlinks // 100)
 
 
@@ -163,3 +178,30 @@ def test_reunitarize_matches_oracle(storage, tol):
         lat.reunitarize()
         o.reunitarize()
         assert np.max(np.abs(lat.get_links() - o.U)) < tol
+
+
+@pytest.mark.parametrize("glue", [0b1111, 0b1000])
+def test_two_couplings_one_sweep(glue):
+    """DLT with beta0 != beta1 (Sec. 2.2): FP64 link by link against the
+    oracle; FP32 within 2e-5 - the beta-weighted staple sums terms of size
+    beta_p, so its float rounding is relatively larger than for one beta
+    (worst measured 1.01e-5 on 1024 links)."""
+    g = dict(dims=[4, 2, 4, 4], nlayers=2, glue_mask=glue)
+    o = oracle_lattice(g).hot_start(19)
+    start = o.U.copy()
+    o.sweep(6.0, 2, 5, n=1, beta1=4.2)
+    with gpu_lattice(g, su3.SU3_FP64_18, beta=6.0, beta1=4.2, seed=5, hits=2) as lat:
+        lat.set_links(start)
+        lat.sweep(1)
+        assert np.max(np.abs(lat.get_links() - o.U)) <= FP64_TOL
+    o2 = oracle_lattice(g)
+    with gpu_lattice(g, su3.SU3_FP32_12, beta=6.0, beta1=4.2, seed=5, hits=2) as lat:
+        lat.set_links(start)
+        start32 = lat.get_links()
+        o2.U[...] = start32
+        margins = np.full(o2.nlinks, np.inf)
+        o2.sweep(6.0, 2, 5, n=1, beta1=4.2, margins=margins)
+        sens = _sensitivity(lambda: oracle_lattice(g), start32, beta=6.0, hits=2, seed=5, n=1, beta1=4.2)
+        lat.sweep(1)
+        counted = _flip_check(lat.get_links(), o2.U, margins, sens, 2 * FP32_TOL)
+    assert counted <= max(2, o2.nlinks // 100)
