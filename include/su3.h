@@ -80,6 +80,8 @@ typedef struct su3_config {
   size_t link_buffer_bytes;     /* its size; must be >= su3_link_bytes() */
   double beta1;                 /* DLT with two couplings (Sec. 2.2): beta of the plaquettes with a link in
                                    layer 1; < 0 (the default of su3_config_init): equal to beta */
+  int32_t ndiv[SU3_MAX_D];      /* sublattices per direction (the paper's MPI sublattices, Sec. 2.4, run on
+                                   one device); 0 or 1: undivided.  See su3_lattice_create_ex. */
 } su3_config;
 
 typedef struct su3_lattice su3_lattice;
@@ -88,7 +90,8 @@ typedef struct su3_lattice su3_lattice;
  * FP64_18, cold, hits=2, no automatic re-unitarisation or measurement. */
 void su3_config_init(su3_config *cfg);
 
-/* Device bytes the links of cfg need (0 if cfg is invalid). */
+/* Device bytes the links of cfg need (0 if cfg is invalid); for a divided
+ * lattice (ndiv) the sublattice boxes plus the undivided copy. */
 size_t su3_link_bytes(const su3_config *cfg);
 
 /* Create a lattice: torus or DLT of the given extents, cold start, FP64_18
@@ -101,7 +104,23 @@ su3_status su3_lattice_create(int D, const int *dims, su3_boundary boundary, dou
  * 2..SU3_MAX_D, an extent is odd or < 2, beta < 0, hits < 1, a period does
  * not divide its extent (or is odd), or the caller buffer is too small;
  * ENOMEM when the device allocation fails.  The start configuration is
- * written before return (asynchronously on the stream). */
+ * written before return (asynchronously on the stream).
+ *
+ * Sublattice decomposition (ndiv[i] > 1 for some i; Sec. 2.4): the lattice
+ * is cut into ndiv[i] sublattices along direction i, each of interior
+ * extent n^i / ndiv[i] (even, >= 2, else EINVAL).  Every sublattice keeps
+ * its links in its own box with one halo layer on both sides of each cut
+ * direction; after every tick that changes links a halo kernel copies the
+ * changed links (faces, and the corner links when two or more directions
+ * are cut) from the sublattice that owns them.  The random numbers are
+ * keyed by the undivided site, so results are bitwise those of the
+ * undivided lattice.  Not with a caller-owned link buffer, ensembles or
+ * the server, nor with two couplings on a DLT cut along a glued direction
+ * (EINVAL).  The launch variant is fixed (su3_set_launch picks threads and
+ * CTAs only); measurements recorded by measure_every hold NaN Polyakov
+ * loops when the time direction is cut (su3_polyakov is exact in every
+ * case: it reads the undivided layout).  su3_lattice_info reports the
+ * bytes of the boxes; an undivided copy of the links is kept besides. */
 su3_status su3_lattice_create_ex(const su3_config *cfg, su3_lattice **out);
 
 /* Release the handle and its device memory (not a caller-owned buffer). */

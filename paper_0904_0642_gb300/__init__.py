@@ -55,7 +55,7 @@ class su3_config(Structure):
         ("beta", c_double), ("seed", c_uint64), ("storage", c_int32), ("start", c_int32), ("hits", c_int32),
         ("reunit_every", c_int32), ("measure_every", c_int32), ("measure_capacity", c_int32),
         ("layer_blind", c_int32), ("rng_period", c_int32 * MAX_D), ("stream", c_void_p), ("link_buffer", c_void_p),
-        ("link_buffer_bytes", c_size_t), ("beta1", c_double),
+        ("link_buffer_bytes", c_size_t), ("beta1", c_double), ("ndiv", c_int32 * MAX_D),
     ]
 
 
@@ -303,7 +303,7 @@ def su3_version() -> str:
 
 def make_config(dims, boundary=SU3_PBC, beta=6.0, seed=1, storage=SU3_FP64_18, start=SU3_START_COLD, hits=2,
                 glue_mask=0, reunit_every=0, measure_every=0, measure_capacity=0, layer_blind=False,
-                rng_period=None, stream=None, buffer=None, beta1=None) -> su3_config:
+                rng_period=None, stream=None, buffer=None, beta1=None, ndiv=None) -> su3_config:
     c = su3_config_init()
     c.D = len(dims)
     for i, n in enumerate(dims):
@@ -323,6 +323,9 @@ def make_config(dims, boundary=SU3_PBC, beta=6.0, seed=1, storage=SU3_FP64_18, s
     if rng_period is not None:
         for i, p in enumerate(rng_period):
             c.rng_period[i] = int(p)
+    if ndiv is not None:  # sublattices per direction (Sec. 2.4), on one device
+        for i, k in enumerate(ndiv):
+            c.ndiv[i] = int(k)
     sh = _stream_handle(stream)
     c.stream = sh
     if buffer is not None:  # a CUDA tensor (torch) or (ptr, nbytes)

@@ -95,7 +95,37 @@ static su3_status validate(const su3_config *c) {
   if (c->reunit_every < 0 || c->measure_every < 0 || c->measure_capacity < 0)
     return fail(SU3_EINVAL, "negative cadence or capacity");
   if (c->glue_mask < 0 || c->glue_mask >= (1 << c->D)) return fail(SU3_EINVAL, "glue_mask=%d out of range", c->glue_mask);
+  long long Vbox = 1;
+  for (int i = 0; i < SU3_MAX_D; ++i) {
+    const int k = c->ndiv[i];
+    if (k < 0) return fail(SU3_EINVAL, "ndiv[%d]=%d < 0", i, k);
+    if (i >= c->D) {
+      if (k > 1) return fail(SU3_EINVAL, "ndiv[%d]=%d for a direction beyond D=%d", i, k, c->D);
+      continue;
+    }
+    if (k > 1) {
+      if (c->dims[i] % k || (c->dims[i] / k) & 1)
+        return fail(SU3_EINVAL, "ndiv[%d]=%d: the sublattice extent n^%d/ndiv = %d/%d must be an even integer", i, k,
+                    i + 1, c->dims[i], k);
+      if (c->link_buffer) return fail(SU3_EINVAL, "a divided lattice keeps its own link storage (no link_buffer)");
+      const int glued = c->boundary == SU3_DLT && (c->glue_mask ? (c->glue_mask >> i) & 1 : 1);
+      if (glued && c->beta1 >= 0.0 && c->beta1 != c->beta)
+        return fail(SU3_EINVAL, "two couplings on a DLT cut along glued direction %d are not supported", i);
+      Vbox *= c->dims[i] / k + 2;
+      Vbox *= k;
+    } else {
+      Vbox *= c->dims[i];
+    }
+  }
+  if (Vbox * layers * c->D * 9 >= 0x7fffffffLL)
+    return fail(SU3_EINVAL, "divided lattice too large: its boxes must stay below 2^31 16-byte vectors");
   return SU3_OK;
+}
+
+static bool divided(const su3_config *c) {
+  for (int i = 0; i < c->D; ++i)
+    if (c->ndiv[i] > 1) return true;
+  return false;
 }
 
 static int nq_of(int storage) { return storage == SU3_FP64_18 ? 9 : 3; }
@@ -107,11 +137,23 @@ static size_t link_bytes_of(const su3_config *c) {
   return (size_t)layers * c->D * V * nq_of(c->storage) * 16;
 }
 
+// Bytes of the sublattice boxes of a divided lattice (interiors and halos).
+static size_t box_bytes_of(const su3_config *c) {
+  size_t nb = 1, Vpad = 1;
+  for (int i = 0; i < c->D; ++i) {
+    const int k = c->ndiv[i] > 1 ? c->ndiv[i] : 1;
+    nb *= (size_t)k;
+    Vpad *= (size_t)(c->dims[i] / k + (k > 1 ? 2 : 0));
+  }
+  const int layers = c->boundary == SU3_DLT ? 2 : 1;
+  return (size_t)layers * c->D * nb * Vpad * nq_of(c->storage) * 16;
+}
+
 extern "C" size_t su3_link_bytes(const su3_config *c) {
   std::string saved = g_err;
   if (validate(c) != SU3_OK) return 0;
   g_err = saved;
-  return link_bytes_of(c);
+  return divided(c) ? box_bytes_of(c) + link_bytes_of(c) : link_bytes_of(c);
 }
 
 // ------------------------------------------------------------------ chains and the engine
@@ -143,6 +185,12 @@ struct Chain {
   size_t link_bytes = 0;
   size_t bytes_total = 0;  // device bytes held (links if owned + scratch)
   uint64_t job_id = 0;     // server only
+  // divided into sublattice boxes: an undivided copy of the links serves the
+  // start, link I/O and host measurements
+  bool sub = false;
+  void *plain = nullptr;
+  ChainDesc pdesc{};
+  ChainDesc *d_pdesc = nullptr;
 };
 
 static void fill_desc(Chain &ch, int tile) {
@@ -194,6 +242,39 @@ static void fill_desc(Chain &ch, int tile) {
       while ((1 << d.shift[i]) < c.dims[i]) ++d.shift[i];
     }
   }
+  // undivided defaults, then the sublattice boxes when the lattice is cut
+  d.nb = 1;
+  d.Vn = d.Vh;
+  d.tiles_per_vl = d.tiles_per_layer;
+  for (int i = 0; i < kMaxD; ++i) {
+    d.idims[i] = d.dims[i];
+    d.hpad[i] = 0;
+    d.bdiv[i] = 1;
+    d.gstride[i] = d.stride[i];
+  }
+  if (divided(&c)) {
+    int nb = 1, Vpad = 1, Vint = 1;
+    for (int i = 0; i < kMaxD; ++i) {
+      if (i < c.D && c.ndiv[i] > 1) {
+        d.bdiv[i] = c.ndiv[i];
+        d.idims[i] = c.dims[i] / c.ndiv[i];
+        d.hpad[i] = 1;
+      }
+      d.dims[i] = d.idims[i] + 2 * d.hpad[i];  // the padded box
+      d.stride[i] = Vpad;
+      if (i < c.D) {
+        nb *= d.bdiv[i];
+        Vpad *= d.dims[i];
+        Vint *= d.idims[i];
+      }
+    }
+    d.nb = nb;
+    d.Vh = Vpad / 2;
+    d.Vn = Vint / 2;
+    d.tiles_per_vl = (d.Vn + tile - 1) / tile;
+    d.tiles_per_layer = nb * d.tiles_per_vl;
+    d.pow2 = 0;
+  }
 
   d.beta_f = (float)c.beta;
   d.beta_d = c.beta;
@@ -204,9 +285,20 @@ static void fill_desc(Chain &ch, int tile) {
   d.action_factor = -(d.weighted ? 1.0 : c.beta) / 3.0;  // weighted: the staples carry the couplings
 }
 
+// The undivided layout of a divided chain: a descriptor over ch.plain that
+// shares the chain's scratch (partial sums sized for both).
+static void fill_plain(Chain &ch, int tile) {
+  Chain tmp = ch;
+  for (int i = 0; i < SU3_MAX_D; ++i) tmp.cfg.ndiv[i] = 0;
+  tmp.links = ch.plain;
+  fill_desc(tmp, tile);
+  ch.pdesc = tmp.desc;
+}
+
 struct Engine {
   int storage = SU3_FP64_18;
   bool weighted_any = false;  // some chain has two couplings: the tick kernel's weighted form
+  bool sub_any = false;       // the (only) chain is divided into sublattice boxes
   cudaStream_t stream = nullptr;
   std::vector<Chain> chains;
   // device mirrors
@@ -258,7 +350,7 @@ struct Engine {
       CU(cudaEventCreate(&p.a));
       CU(cudaEventCreate(&p.b));
       CU(cudaEventRecord(p.a, stream));
-      CU(launch_tick(storage, variant, weighted_any, args(), grid, block, stream));
+      TRY(one_tick(grid));
       CU(cudaEventRecord(p.b, stream));
       prof_pending.push_back(p);
       if (s.active) {
@@ -317,6 +409,10 @@ struct Engine {
 
   static void free_chain(Chain &ch) {
     if (ch.own_links) cudaFree(ch.links);
+    cudaFree(ch.plain);
+    cudaFree(ch.d_pdesc);
+    ch.plain = nullptr;
+    ch.d_pdesc = nullptr;
     cudaFree(ch.results);
     cudaFree(ch.partials);
     cudaFree(ch.counters);
@@ -346,7 +442,20 @@ struct Engine {
   su3_status add_chain(const su3_config &cfg, Chain &out) {
     Chain ch;
     ch.cfg = cfg;
+    ch.sub = divided(&cfg);
     ch.link_bytes = link_bytes_of(&cfg);
+    if (ch.sub) {
+      // the sublattice boxes, and the undivided copy
+      fill_desc(ch, 32);
+      ch.link_bytes = box_bytes_of(&cfg);
+      const size_t pb = link_bytes_of(&cfg);
+      if (cudaMalloc(&ch.plain, pb) != cudaSuccess) return fail(SU3_ENOMEM, "cudaMalloc of %zu bytes failed", pb);
+      if (cudaMalloc(&ch.d_pdesc, sizeof(ChainDesc)) != cudaSuccess) {
+        free_chain(ch);
+        return fail(SU3_ENOMEM, "descriptor allocation failed");
+      }
+      ch.bytes_total += pb + sizeof(ChainDesc);
+    }
     if (cfg.link_buffer) {
       if (cfg.link_buffer_bytes < ch.link_bytes)
         return fail(SU3_EINVAL, "link_buffer holds %zu bytes, %zu needed", cfg.link_buffer_bytes, ch.link_bytes);
@@ -355,12 +464,20 @@ struct Engine {
       ch.own_links = false;
     } else {
       cudaError_t e = cudaMalloc(&ch.links, ch.link_bytes);
-      if (e != cudaSuccess) return fail(SU3_ENOMEM, "cudaMalloc of %zu link bytes: %s", ch.link_bytes, cudaGetErrorString(e));
+      if (e != cudaSuccess) {
+        free_chain(ch);
+        return fail(SU3_ENOMEM, "cudaMalloc of %zu link bytes: %s", ch.link_bytes, cudaGetErrorString(e));
+      }
       ch.own_links = true;
       ch.bytes_total += ch.link_bytes;
     }
     fill_desc(ch, 32);  // partials sized for the narrowest tile
-    const size_t npart = (size_t)ch.desc.nlayers * ch.desc.tiles_per_layer * kPartVals;
+    size_t ntiles = (size_t)ch.desc.nlayers * ch.desc.tiles_per_layer;
+    if (ch.sub) {
+      fill_plain(ch, 32);
+      ntiles = std::max(ntiles, (size_t)ch.pdesc.nlayers * ch.pdesc.tiles_per_layer);
+    }
+    const size_t npart = ntiles * kPartVals;
     const size_t nres = (size_t)ch.desc.result_cap * (ch.desc.nlayers + 1) * kMeasVals;
     cudaError_t e1 = cudaMalloc(&ch.partials, npart * sizeof(double));
     cudaError_t e2 = cudaMalloc(&ch.results, nres * sizeof(double));
@@ -370,7 +487,7 @@ struct Engine {
       return fail(SU3_ENOMEM, "scratch allocation failed");
     }
     ch.bytes_total += npart * sizeof(double) + nres * sizeof(double) + 16;
-    ch.n_action_slots = ch.desc.nlayers * ((ch.desc.Vh + 31) / 32);
+    ch.n_action_slots = ch.desc.nlayers * ch.desc.nb * ((ch.desc.Vn + 31) / 32);
     if (cudaMalloc(&ch.action_slots, (size_t)ch.n_action_slots * sizeof(double)) != cudaSuccess) {
       free_chain(ch);
       return fail(SU3_ENOMEM, "action bookkeeping allocation failed");
@@ -380,8 +497,10 @@ struct Engine {
     CU(cudaMemsetAsync(ch.counters, 0, 2 * sizeof(unsigned long long), stream));
     CU(cudaMemsetAsync(ch.results, 0, nres * sizeof(double), stream));
     fill_desc(ch, block);
+    if (ch.sub) fill_plain(ch, block);
     ch.state = ChainState{};
     ch.state.active = 0;
+    ch.state.prev_stage = -1;
     out = ch;
     return SU3_OK;
   }
@@ -392,7 +511,19 @@ struct Engine {
     CU(cudaMallocAsync(&dd, sizeof(ChainDesc), stream));
     CU(cudaMemcpyAsync(dd, &ch.desc, sizeof(ChainDesc), cudaMemcpyHostToDevice, stream));
     const size_t nlinks = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
-    CU(launch_start(storage, dd, nlinks, ch.cfg.start == SU3_START_HOT, stream));
+    if (ch.sub) {
+      // start the undivided layout, scatter it into the boxes, fill every halo
+      CU(cudaMemcpyAsync(ch.d_pdesc, &ch.pdesc, sizeof(ChainDesc), cudaMemcpyHostToDevice, stream));
+      CU(launch_start(storage, ch.d_pdesc, nlinks, ch.cfg.start == SU3_START_HOT, stream));
+      CU(launch_sub_copy(storage, dd, ch.d_pdesc, nlinks, 1, stream));
+      ChainState *ds = nullptr;
+      CU(cudaMallocAsync(&ds, sizeof(ChainState), stream));
+      CU(cudaMemsetAsync(ds, 0, sizeof(ChainState), stream));
+      CU(launch_halo(storage, dd, ds, 1, (long long)ch.desc.nlayers * ch.desc.nb * 2 * ch.desc.Vh, stream));
+      CU(cudaFreeAsync(ds, stream));
+    } else {
+      CU(launch_start(storage, dd, nlinks, ch.cfg.start == SU3_START_HOT, stream));
+    }
     CU(cudaFreeAsync(dd, stream));
     CU(cudaStreamSynchronize(stream));  // the host ChainDesc copy is freed with it
     return SU3_OK;
@@ -409,10 +540,18 @@ struct Engine {
     }
     total_tiles = tiles;
     if (ctas_per_sm <= 0 && tiles != old_tiles) drop_graph();  // the grid follows the tile count
-    bool w = false;
-    for (auto &ch : chains) w = w || ch.desc.weighted;
-    if (w != weighted_any) {  // another kernel form: the captured graph is stale
+    bool w = false, sb = false;
+    for (auto &ch : chains) {
+      w = w || ch.desc.weighted;
+      sb = sb || ch.sub;
+      if (ch.sub) {
+        fill_plain(ch, block);
+        CU(cudaMemcpyAsync(ch.d_pdesc, &ch.pdesc, sizeof(ChainDesc), cudaMemcpyHostToDevice, stream));
+      }
+    }
+    if (w != weighted_any || sb != sub_any) {  // another kernel form: the captured graph is stale
       weighted_any = w;
+      sub_any = sb;
       drop_graph();
     }
     if (chains.size() > chain_cap) {
@@ -500,10 +639,46 @@ struct Engine {
 
   EngineArgs args() const { return EngineArgs{d_desc, d_state, d_hdr, d_tile_chain}; }
 
+  // Sites of all sublattice boxes of a divided chain (the only chain of its engine).
+  long long padded_sites() const {
+    const ChainDesc &d = chains[0].desc;
+    return (long long)d.nlayers * d.nb * 2 * d.Vh;
+  }
+
+  // One tick, and for a divided chain the halo refresh of what it changed.
+  su3_status one_tick(int grid) {
+    CU(launch_tick(storage, variant, weighted_any, sub_any, args(), grid, block, stream));
+    if (sub_any) CU(launch_halo(storage, d_desc, d_state, 0, padded_sites(), stream));
+    return SU3_OK;
+  }
+
+  // Divided chains: undivided layout <-> boxes (to_sub = 1: scatter and
+  // refresh every halo).  d_desc must hold the chain's descriptor.
+  su3_status sub_sync(size_t c, int to_sub) {
+    Chain &ch = chains[c];
+    const size_t nlinks = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
+    CU(launch_sub_copy(storage, d_desc + c, ch.d_pdesc, nlinks, to_sub, stream));
+    if (to_sub) CU(launch_halo(storage, d_desc + c, d_state + c, 1, padded_sites(), stream));
+    return SU3_OK;
+  }
+
+  // The descriptor that measurement and link I/O kernels read: the chain's
+  // own, or (divided chain) its undivided copy after a gather.
+  su3_status io_desc(size_t c, ChainDesc **dd) {
+    Chain &ch = chains[c];
+    if (!ch.sub) {
+      *dd = d_desc + c;
+      return SU3_OK;
+    }
+    TRY(sub_sync(c, 0));
+    *dd = ch.d_pdesc;
+    return SU3_OK;
+  }
+
   su3_status tick_direct(int n) {
     int grid = 0;
     TRY(grid_size(&grid));
-    for (int i = 0; i < n; ++i) CU(launch_tick(storage, variant, weighted_any, args(), grid, block, stream));
+    for (int i = 0; i < n; ++i) TRY(one_tick(grid));
     return SU3_OK;
   }
 
@@ -516,7 +691,8 @@ struct Engine {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kGraphTicks; ++i) {
-      cudaError_t e = launch_tick(storage, variant, weighted_any, args(), grid, block, stream);
+      cudaError_t e = launch_tick(storage, variant, weighted_any, sub_any, args(), grid, block, stream);
+      if (e == cudaSuccess && sub_any) e = launch_halo(storage, d_desc, d_state, 0, padded_sites(), stream);
       if (e != cudaSuccess) {
         cudaStreamEndCapture(stream, &g);
         if (g) cudaGraphDestroy(g);
@@ -591,7 +767,10 @@ struct Engine {
     Chain &ch = chains[c];
     const int nvals = (ch.desc.nlayers + 1) * kMeasVals;
     if (!d_meas_out) CU(cudaMalloc(&d_meas_out, 3 * kMeasVals * sizeof(double)));
-    CU(launch_measure(storage, d_desc + c, ch.desc.nlayers * ch.desc.tiles_per_layer, block, d_meas_out, stream));
+    ChainDesc *dd = nullptr;
+    TRY(io_desc(c, &dd));
+    const ChainDesc &md = ch.sub ? ch.pdesc : ch.desc;
+    CU(launch_measure(storage, dd, md.nlayers * md.tiles_per_layer, block, d_meas_out, stream));
     CU(cudaMemcpyAsync(h_pinned, d_meas_out, nvals * sizeof(double), cudaMemcpyDeviceToHost, stream));
     CU(cudaStreamSynchronize(stream));
     std::memcpy(host_out, h_pinned, nvals * sizeof(double));
@@ -604,8 +783,10 @@ struct Engine {
     const size_t nlinks = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
     if (!host || n < nlinks * 18) return fail(SU3_EINVAL, "host buffer holds %zu doubles, %zu needed", n, nlinks * 18);
     double *canon = nullptr;
+    ChainDesc *dd = nullptr;
+    TRY(io_desc(c, &dd));
     CU(cudaMallocAsync(&canon, nlinks * 18 * sizeof(double), stream));
-    CU(launch_convert(storage, d_desc + c, nlinks, canon, 1, stream));
+    CU(launch_convert(storage, dd, nlinks, canon, 1, stream));
     CU(cudaMemcpyAsync(host, canon, nlinks * 18 * sizeof(double), cudaMemcpyDeviceToHost, stream));
     CU(cudaFreeAsync(canon, stream));
     CU(cudaStreamSynchronize(stream));
@@ -620,7 +801,8 @@ struct Engine {
     double *canon = nullptr;
     CU(cudaMallocAsync(&canon, nlinks * 18 * sizeof(double), stream));
     CU(cudaMemcpyAsync(canon, host, nlinks * 18 * sizeof(double), cudaMemcpyHostToDevice, stream));
-    CU(launch_convert(storage, d_desc + c, nlinks, canon, 0, stream));
+    CU(launch_convert(storage, ch.sub ? ch.d_pdesc : d_desc + c, nlinks, canon, 0, stream));
+    if (ch.sub) TRY(sub_sync(c, 1));  // scatter into the boxes, refresh every halo
     CU(cudaFreeAsync(canon, stream));
     CU(cudaStreamSynchronize(stream));
     return action_reset(c);  // the links changed without bookkeeping
@@ -802,7 +984,10 @@ extern "C" su3_status su3_measure_async(su3_lattice *lat, double *device_out) {
   Engine &e = lat->eng;
   if (e.tiles_dirty) TRY(e.rebuild());
   Chain &ch = e.chains[0];
-  CU(launch_measure(e.storage, e.d_desc, ch.desc.nlayers * ch.desc.tiles_per_layer, e.block, device_out, e.stream));
+  ChainDesc *dd = nullptr;
+  TRY(e.io_desc(0, &dd));
+  const ChainDesc &md = ch.sub ? ch.pdesc : ch.desc;
+  CU(launch_measure(e.storage, dd, md.nlayers * md.tiles_per_layer, e.block, device_out, e.stream));
   return SU3_OK;
 }
 
@@ -940,11 +1125,12 @@ static su3_status autotune_engine(Engine &e, int *variant, int *threads, int *ct
   int best_v = saved_var, best_t = saved_block, best_c = saved_ctas;
   const int cand_t[] = {64, 128, 256};
   su3_status st = SU3_OK;
-  for (int v = 0; v < tick_variants(e.storage) && st == SU3_OK; ++v)
+  const int nvar = e.sub_any ? 1 : tick_variants(e.storage);  // a divided chain has one kernel form
+  for (int v = 0; v < nvar && st == SU3_OK; ++v)
     for (int t : cand_t) {
       if (t > tick_max_threads(e.storage, v)) continue;
       int occ = 0;
-      if (tick_occupancy(e.storage, v, e.weighted_any, t, &occ) != cudaSuccess || occ < 1) continue;
+      if (tick_occupancy(e.storage, v, e.weighted_any, e.sub_any, t, &occ) != cudaSuccess || occ < 1) continue;
       // 0 = one CTA per tile, then persistent grids of 1, 2, 4, ..., occ CTAs per SM
       for (int c = 0; c <= occ && st == SU3_OK; c = (c == 0) ? 1 : ((c < occ && 2 * c > occ) ? occ : 2 * c)) {
         if ((st = e.set_launch(v, t, c)) != SU3_OK) break;
@@ -1008,6 +1194,7 @@ extern "C" su3_status su3_measure_noalloc(const su3_config *cfg, const void *lin
   const int block = 256;
   Chain ch;  // a descriptor only: no device memory is touched or allocated here
   ch.cfg = *cfg;
+  for (int i = 0; i < SU3_MAX_D; ++i) ch.cfg.ndiv[i] = 0;  // the caller's links are undivided
   ch.links = const_cast<void *>(links);
   fill_desc(ch, block);
   const long long tiles = (long long)ch.desc.tiles_per_layer * ch.desc.nlayers;
@@ -1033,6 +1220,7 @@ extern "C" su3_status su3_ensemble_create(const su3_config *cfgs, int nchains, v
   for (int c = 0; c < nchains; ++c) {
     TRY(validate(&cfgs[c]));
     if (cfgs[c].storage != cfgs[0].storage) return fail(SU3_EINVAL, "all chains of an ensemble share one storage");
+    if (divided(&cfgs[c])) return fail(SU3_EINVAL, "chain %d: ensembles take undivided lattices (ndiv)", c);
   }
   auto *ens = new su3_ensemble();
   su3_status st = ens->eng.init(cfgs[0].storage, (cudaStream_t)stream);
@@ -1186,7 +1374,7 @@ extern "C" su3_status su3_server_create(size_t hbm_budget_bytes, int max_slots, 
     // persistent grid: its size does not depend on the resident jobs, so the
     // captured graph of ticks survives admissions and retirements
     int occ = 0;
-    if (tick_occupancy(SU3_FP32_12, srv->eng.variant, false, srv->eng.block, &occ) != cudaSuccess || occ < 1) occ = 1;
+    if (tick_occupancy(SU3_FP32_12, srv->eng.variant, false, false, srv->eng.block, &occ) != cudaSuccess || occ < 1) occ = 1;
     srv->eng.ctas_per_sm = occ;
   }
   srv->t0 = std::chrono::steady_clock::now();
@@ -1203,6 +1391,7 @@ extern "C" su3_status su3_server_submit(su3_server *srv, const su3_job *job, uin
   c.link_buffer_bytes = 0;
   c.storage = SU3_FP32_12;
   TRY(validate(&c));
+  if (divided(&c)) return fail(SU3_EINVAL, "the server takes undivided lattices (ndiv)");
   if (job->sweeps < 1) return fail(SU3_EINVAL, "sweeps=%d < 1", job->sweeps);
   if (job_bytes(c) > srv->budget) return fail(SU3_ENOMEM, "job needs %zu bytes, budget is %zu", job_bytes(c), srv->budget);
   std::lock_guard<std::mutex> lk(srv->mu);

@@ -56,6 +56,20 @@ struct ChainDesc {
   int32_t spatial_per_layer; // V / n^D (Polyakov lines per layer)
   int32_t pow2;              // 1: every extent is a power of two (coordinates by shifts)
   int32_t shift[kMaxD];      // log2 n^i when pow2
+  // Sublattice decomposition on one device (the paper's MPI sublattices,
+  // Sec. 2.4): nb sublattices per layer, each stored as its own padded box
+  // (interior idims plus one halo layer on both sides where hpad = 1), the
+  // boxes side by side as virtual layers vl = layer * nb + block.  In that
+  // case dims / stride / Vh describe the padded box, V the undivided layer
+  // and gstride its strides (random-number site key).  Undivided: nb = 1,
+  // idims = dims, hpad = 0, bdiv = 1, Vn = Vh.
+  int32_t nb;
+  int32_t tiles_per_vl;      // ceil(Vn / tile); tiles_per_layer = nb * tiles_per_vl
+  int32_t Vn;                // sites of one colour updated per virtual layer
+  int32_t idims[kMaxD];      // interior extents
+  int32_t hpad[kMaxD];       // 1: divided direction, one halo layer on each side
+  int32_t bdiv[kMaxD];       // sublattices per direction
+  int32_t gstride[kMaxD];    // strides of the undivided layer
   float beta_f;
   double beta_d;
   // DLT with two couplings (Sec. 2.2): weighted = 1 when beta1 != beta; a
@@ -73,7 +87,8 @@ struct ChainState {
   uint32_t target;         // the chain goes idle at the start of this sweep
   int32_t active;          // 1: advancing; 0: idle
   uint32_t n_meas;         // measurements recorded
-  int32_t pad[3];
+  int32_t prev_stage;      // stage run by the last tick (-1: none); read by the halo refresh
+  int32_t pad[2];
 };
 
 struct EngineHeader {

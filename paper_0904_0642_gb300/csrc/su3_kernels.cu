@@ -27,8 +27,38 @@ struct SiteGeo {
 // Coordinates of the site of colour `colour` at checkerboard index jj
 // (eqs. xD, x^i, i_c): the even lexicographic index 2 jj shares its row
 // with the odd one, and the colour fixes which of the two it is.
+// SUB (sublattice boxes): jj counts the interior sites of the box; the
+// returned coordinates and index are those of the padded box.  Sublattice
+// origins are even, so the colour is the colour of the undivided lattice.
+template <bool SUB = false>
 __device__ __forceinline__ SiteGeo site_of(const ChainDesc &d, int layer, int colour, int jj) {
   SiteGeo g;
+  if constexpr (SUB) {
+    int r = 2 * jj, par = colour;
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i) {
+      if (i < d.D) {
+        const int n = d.idims[i];
+        const int q = r / n;
+        g.x[i] = r - q * n;
+        r = q;
+        if (i > 0) par += g.x[i];
+      } else {
+        g.x[i] = 0;
+      }
+    }
+    g.x[0] += par & 1;
+    int sp = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i)
+      if (i < d.D) {
+        g.x[i] += d.hpad[i];
+        sp += g.x[i] * d.stride[i];
+      }
+    g.s = sp;
+    g.layer = layer;
+    return g;
+  }
   int r = 2 * jj;
   int par = colour;
   if (d.pow2) {
@@ -85,9 +115,46 @@ __device__ __forceinline__ void step_bwd(const ChainDesc &d, int xnu, int nu, in
   }
 }
 
+// The layer reached by a step with layer flip f: for sublattice boxes the
+// virtual layer of the same sublattice in the other layer.
+template <bool SUB>
+__device__ __forceinline__ int lflip(const ChainDesc &d, int l, int f) {
+  if constexpr (SUB)
+    return f ? (l < d.nb ? l + d.nb : l - d.nb) : l;
+  else
+    return l ^ f;
+}
+
+// 1 when (virtual) layer l belongs to layer 1 of the double-layered torus.
+template <bool SUB>
+__device__ __forceinline__ int in_layer1(const ChainDesc &d, int l) {
+  if constexpr (SUB)
+    return l >= d.nb ? 1 : 0;
+  else
+    return l;
+}
+
 // Random-number site key: layer * V + i_s - 1, or the site number of
 // (x mod period) on the period lattice (identical numbers on sublattices).
+// SUB: from the coordinates in the undivided lattice, so that a divided
+// lattice draws the same numbers as the undivided one.
+template <bool SUB = false>
 __device__ __forceinline__ uint32_t site_key(const ChainDesc &d, const SiteGeo &g) {
+  if constexpr (SUB) {
+    const int L = g.layer / d.nb;
+    int b = g.layer - L * d.nb;
+    const int lay = (d.nlayers == 2 && !d.layer_blind) ? L : 0;
+    int key = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i)
+      if (i < d.D) {
+        const int bc = b % d.bdiv[i];
+        b /= d.bdiv[i];
+        const int gx = bc * d.idims[i] + g.x[i] - d.hpad[i];
+        key += d.custom_period ? (gx % d.period[i]) * d.pstride[i] : gx * d.gstride[i];
+      }
+    return (uint32_t)(lay * (d.custom_period ? d.Vp : d.V) + key);
+  }
   const int lay = (d.nlayers == 2 && !d.layer_blind) ? g.layer : 0;
   if (!d.custom_period) return (uint32_t)(lay * d.V + g.s);
   int key = 0;
@@ -108,7 +175,7 @@ __device__ __forceinline__ int sel(const int (&x)[kMaxD], int i) {
 // ------------------------------------------------------------------ one link update
 
 // The staples of one direction nu added to A.
-template <class S, bool WT>
+template <class S, bool WT, bool SUB>
 __device__ __forceinline__ void add_staples(const ChainDesc &d, const SiteGeo &g, int colour, int mu, int nu, int xnu,
                                             int sp, int lp, M3<typename S::R> &A) {
   using R = typename S::R;
@@ -116,9 +183,9 @@ __device__ __forceinline__ void add_staples(const ChainDesc &d, const SiteGeo &g
   int offn, fln, offm, flm;
   step_fwd(d, xnu, nu, offn, fln);
   step_bwd(d, xnu, nu, offm, flm);
-  const int sn = g.s + offn, ln = layer ^ fln;       // x + nu
-  const int sm = g.s + offm, lm = layer ^ flm;       // x - nu
-  const int spm = sp + offm, lpm = lp ^ flm;         // x + mu - nu
+  const int sn = g.s + offn, ln = lflip<SUB>(d, layer, fln);  // x + nu
+  const int sm = g.s + offm, lm = lflip<SUB>(d, layer, flm);  // x - nu
+  const int spm = sp + offm, lpm = lflip<SUB>(d, lp, flm);    // x + mu - nu
   // upper staple U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ = a (c b)^+, all factors SU(3):
   // two rows of each product, the third from the cross product
   const M3<R> b = S::load(plane_ptr<S>(d, ln, oc, mu), Vh, sn >> 1);       // U_mu(x+nu)
@@ -133,7 +200,7 @@ __device__ __forceinline__ void add_staples(const ChainDesc &d, const SiteGeo &g
   const bool weighted = WT && d.weighted;
   const R b0 = sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d, b1 = sizeof(R) == 4 ? (R)d.beta1_f : (R)d.beta1_d;
   if (weighted)
-    acc_su3_2rows_w(A, mul_nd_2(a, cb), (layer | lp | ln) ? b1 : b0);
+    acc_su3_2rows_w(A, mul_nd_2(a, cb), (in_layer1<SUB>(d, layer) | in_layer1<SUB>(d, lp) | in_layer1<SUB>(d, ln)) ? b1 : b0);
   else
     acc_su3_2rows(A, mul_nd_2(a, cb));
   // lower staple U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) = (e f)^+ h
@@ -143,55 +210,58 @@ __device__ __forceinline__ void add_staples(const ChainDesc &d, const SiteGeo &g
   third_row(ef);
   const M3<R> h = S::load(plane_ptr<S>(d, lm, oc, nu), Vh, sm >> 1);       // U_nu(x-nu)
   if (weighted)
-    acc_su3_2rows_w(A, mul_dn_2(ef, h), (lm | lpm | layer) ? b1 : b0);
+    acc_su3_2rows_w(A, mul_dn_2(ef, h), (in_layer1<SUB>(d, lm) | in_layer1<SUB>(d, lpm) | in_layer1<SUB>(d, layer)) ? b1 : b0);
   else
     acc_su3_2rows(A, mul_dn_2(ef, h));
 }
 
 // ROLLED: the loop over staple directions stays a loop (no unrolling), so the
 // compiler cannot hoist later directions' loads; fewer registers, less code.
-template <class S, bool ROLLED, bool WT>
+template <class S, bool ROLLED, bool WT, bool SUB>
 __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, int colour, int mu, int layer, int jj,
                                             uint32_t &nprop, uint32_t &nacc, typename S::R &dretr) {
   using R = typename S::R;
   const int Vh = d.Vh;
-  const SiteGeo g = site_of(d, layer, colour, jj);
+  const SiteGeo g = site_of<SUB>(d, layer, colour, jj);
   int offp, flp;
   step_fwd(d, sel(g.x, mu), mu, offp, flp);
-  const int sp = g.s + offp, lp = layer ^ flp;  // x + mu
+  const int sp = g.s + offp, lp = lflip<SUB>(d, layer, flp);  // x + mu
   const uint2 key = make_uint2(d.seed_lo, d.seed_hi);
-  const uint32_t skey = site_key(d, g);
+  const uint32_t skey = site_key<SUB>(d, g);
 
   M3<R> A = m3_zero<R>();
   if constexpr (ROLLED) {
 #pragma unroll 1
     for (int nu = 0; nu < d.D; ++nu)
-      if (nu != mu) add_staples<S, WT>(d, g, colour, mu, nu, sel(g.x, nu), sp, lp, A);
+      if (nu != mu) add_staples<S, WT, SUB>(d, g, colour, mu, nu, sel(g.x, nu), sp, lp, A);
   } else {
 #pragma unroll
     for (int nu = 0; nu < kMaxD; ++nu)
-      if (nu < d.D && nu != mu) add_staples<S, WT>(d, g, colour, mu, nu, g.x[nu], sp, lp, A);
+      if (nu < d.D && nu != mu) add_staples<S, WT, SUB>(d, g, colour, mu, nu, g.x[nu], sp, lp, A);
   }
   typename S::Vec *pu = plane_ptr<S>(d, layer, colour, mu);
-  M3<R> U = S::load(pu, Vh, jj);
+  const int ju = g.s >> 1;  // jj itself unless the site sits in a padded box
+  M3<R> U = S::load(pu, Vh, ju);
   const R beta = (WT && d.weighted) ? R(1) : (sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d);
   cm_update(U, A, beta, d.hits, key, skey, sweep, colour, mu, nprop, nacc, dretr);
-  S::store(pu, Vh, jj, U);
+  S::store(pu, Vh, ju, U);
 }
 
 
 // ------------------------------------------------------------------ re-unitarisation
 
-template <class S>
+template <class S, bool SUB = false>
 __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int jj) {
   const int Vh = d.Vh;
-  for (int colour = 0; colour < 2; ++colour)
+  for (int colour = 0; colour < 2; ++colour) {
+    const int js = SUB ? (site_of<true>(d, layer, colour, jj).s >> 1) : jj;
     for (int mu = 0; mu < d.D; ++mu) {
       typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
-      M3<double> m = m3_cast<double>(S::load(p, Vh, jj));
+      M3<double> m = m3_cast<double>(S::load(p, Vh, js));
       reunit_d<sizeof(typename S::R) == 4 ? 1 : 2>(m);
-      S::store(p, Vh, jj, m3_cast<typename S::R>(m));
+      S::store(p, Vh, js, m3_cast<typename S::R>(m));
     }
+  }
 }
 
 // ------------------------------------------------------------------ measurements
@@ -202,7 +272,7 @@ __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int j
 // (1/3) Re Tr(U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+) = (1/3) sum_ij
 // Re(P_ij conj(Q_ij)) with P = U_mu(x) U_nu(x+mu), Q = U_nu(x) U_mu(x+nu),
 // taken row by row so that few values are live at once.
-template <class S>
+template <class S, bool SUB = false>
 __device__ __forceinline__ double plaquette_at(const ChainDesc &d, const SiteGeo &g, int colour, int mu, int nu,
                                                int xmu, int xnu) {
   using R = typename S::R;
@@ -210,8 +280,8 @@ __device__ __forceinline__ double plaquette_at(const ChainDesc &d, const SiteGeo
   int offp, flp, offn, fln;
   step_fwd(d, xmu, mu, offp, flp);
   step_fwd(d, xnu, nu, offn, fln);
-  const M3<R> a = S::load(plane_ptr<S>(d, layer ^ flp, oc, nu), Vh, (g.s + offp) >> 1);  // U_nu(x+mu)
-  const M3<R> b = S::load(plane_ptr<S>(d, layer ^ fln, oc, mu), Vh, (g.s + offn) >> 1);  // U_mu(x+nu)
+  const M3<R> a = S::load(plane_ptr<S>(d, lflip<SUB>(d, layer, flp), oc, nu), Vh, (g.s + offp) >> 1);  // U_nu(x+mu)
+  const M3<R> b = S::load(plane_ptr<S>(d, lflip<SUB>(d, layer, fln), oc, mu), Vh, (g.s + offn) >> 1);  // U_mu(x+nu)
   const M3<R> um = S::load(plane_ptr<S>(d, layer, colour, mu), Vh, jj);                  // U_mu(x)
   const M3<R> un = S::load(plane_ptr<S>(d, layer, colour, nu), Vh, jj);                  // U_nu(x)
   R tr = R(0);
@@ -236,34 +306,36 @@ __device__ __forceinline__ double plaquette_at(const ChainDesc &d, const SiteGeo
 // Per thread: the two sites of checkerboard index jj (both colours).  Sums
 // in double: plaquettes split space/time, and Polyakov lines started at
 // x^D = 0 (the line follows the forward time neighbour until it closes).
-template <class S>
+// SUB: plaquettes read the forward halos; a Polyakov line stays inside its
+// sublattice box only when time is undivided, so it is taken only then.
+template <class S, bool SUB = false>
 __device__ __forceinline__ void measure_site(const ChainDesc &d, int layer, int jj, double acc[kPartVals]) {
   using R = typename S::R;
   const int Vh = d.Vh;
   const int D = d.D;
 #pragma unroll 1
   for (int colour = 0; colour < 2; ++colour) {
-    const SiteGeo g = site_of(d, layer, colour, jj);
+    const SiteGeo g = site_of<SUB>(d, layer, colour, jj);
 #pragma unroll 1
     for (int mu = 0; mu < D; ++mu) {
       const int xmu = sel(g.x, mu);
 #pragma unroll 1
       for (int nu = mu + 1; nu < D; ++nu) {
-        const double p = plaquette_at<S>(d, g, colour, mu, nu, xmu, sel(g.x, nu));
+        const double p = plaquette_at<S, SUB>(d, g, colour, mu, nu, xmu, sel(g.x, nu));
         if (nu == D - 1) acc[1] += p; else acc[0] += p;
       }
     }
     const int t = D - 1;
-    if (sel(g.x, t) == 0) {
+    if (sel(g.x, t) == 0 && !(SUB && d.hpad[t])) {
       // Polyakov line through (layer, x, x^D = 0)
-      M3<R> P = S::load(plane_ptr<S>(d, layer, colour, t), Vh, jj);
+      M3<R> P = S::load(plane_ptr<S>(d, layer, colour, t), Vh, g.s >> 1);
       int cs = g.s, cl = layer, cc = colour, xt = 0;
 #pragma unroll 1
       for (int step = 0; step < 2 * d.dims[t]; ++step) {
         int off, fl;
         step_fwd(d, xt, t, off, fl);
         cs += off;
-        cl ^= fl;
+        cl = lflip<SUB>(d, cl, fl);
         cc ^= 1;
         xt = (xt == d.dims[t] - 1) ? 0 : xt + 1;
         if (cs == g.s && cl == layer) break;
@@ -306,7 +378,8 @@ __device__ void finalize_measure(const ChainDesc &d, const double *partials, dou
   double whole[kPartVals] = {0, 0, 0, 0};
   const int D = d.D;
   const double np_s = (double)d.V * (D - 1) * (D - 2) / 2, np_t = (double)d.V * (D - 1);
-  const double nl = (double)d.spatial_per_layer;
+  // Polyakov lines are not taken inside sublattice boxes with divided time
+  const double nl = d.hpad[D - 1] ? __longlong_as_double(0x7ff8000000000000ll) : (double)d.spatial_per_layer;
   for (int layer = 0; layer < d.nlayers; ++layer) {
     double v[kPartVals] = {0, 0, 0, 0};
     for (int t = lane; t < d.tiles_per_layer; t += 32)
@@ -324,7 +397,7 @@ __device__ void finalize_measure(const ChainDesc &d, const double *partials, dou
       o[0] = (v[0] + v[1]) / (np_s + np_t);
       o[1] = np_s > 0 ? v[0] / np_s : 0.0;
       o[2] = v[1] / np_t;
-      o[3] = v[2] / nl;
+      o[3] = v[2] / nl;  // NaN when nl is
       o[4] = v[3] / nl;
     }
   }
@@ -370,6 +443,7 @@ __device__ __forceinline__ void flush_counters(const ChainDesc &d, uint32_t &np,
 // measurement when the completed-sweep count is a multiple of their
 // cadence; the chain goes idle when a sweep would start at its target.
 __device__ __host__ inline void advance_stage(const ChainDesc &d, ChainState &s) {
+  s.prev_stage = s.stage;
   if (s.stage < 2 * d.D) {
     s.stage += 1;
     if (s.stage == 2 * d.D) {
@@ -406,7 +480,9 @@ template <> struct TickBounds<10> { static constexpr int kThreads = 256, kMinBlo
 
 // WT: compiled for engines holding a two-coupling DLT chain (any chain with
 // beta1 != beta); unweighted chains compute identically in both forms.
-template <class S, int V, bool WT>
+// SUB: compiled for a chain divided into sublattice boxes (one chain per
+// engine); a halo refresh follows every launch.
+template <class S, int V, bool WT, bool SUB = false>
 __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBlocks) k_tick(EngineArgs ea) {
   __shared__ ChainDesc sd;
   __shared__ ChainState ss;
@@ -426,25 +502,26 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
     }
     if (!ss.active) continue;
     const int lt = t - sd.tile_base;
-    const int layer = lt / sd.tiles_per_layer;
-    const int jj = (lt - layer * sd.tiles_per_layer) * blockDim.x + threadIdx.x;
-    const bool valid = jj < sd.Vh;
+    const int layer = lt / sd.tiles_per_vl;  // a layer, or a sublattice box of one
+    const int jj = (lt - layer * sd.tiles_per_vl) * blockDim.x + threadIdx.x;
+    const bool valid = jj < sd.Vn;
     if (ss.stage < 2 * sd.D) {
       const int colour = ss.stage / sd.D, mu = ss.stage - colour * sd.D;
       typename S::R dr = 0;  // change of Re Tr(U A), in the kernel's precision
-      if (valid) update_site<S, TickBounds<V>::kRolled, WT>(sd, ss.sweep, colour, mu, layer, jj, np, na, dr);
+      if (valid) update_site<S, TickBounds<V>::kRolled, WT, SUB>(sd, ss.sweep, colour, mu, layer, jj, np, na, dr);
       // book the action change S = sum_p beta_p (1 - Re Tr U_p / 3): each warp
       // owns the slot of its 32 sites, so the one fire-and-forget add per warp
       // meets no other add in this launch and the order of adds is fixed
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) dr += __shfl_down_sync(0xffffffffu, dr, o);
-      if ((threadIdx.x & 31) == 0 && sd.action_slots)
-        atomicAdd(sd.action_slots + layer * ((sd.Vh + 31) >> 5) + (jj >> 5), sd.action_factor * (double)dr);
+      // (a warp of the ragged last tile with no valid site has no slot)
+      if ((threadIdx.x & 31) == 0 && valid && sd.action_slots)
+        atomicAdd(sd.action_slots + layer * ((sd.Vn + 31) >> 5) + (jj >> 5), sd.action_factor * (double)dr);
     } else if (ss.stage == kStageReunit) {
-      if (valid) reunit_site<S>(sd, layer, jj);
+      if (valid) reunit_site<S, SUB>(sd, layer, jj);
     } else {
       double v[kPartVals] = {0, 0, 0, 0};
-      if (valid) measure_site<S>(sd, layer, jj, v);
+      if (valid) measure_site<S, SUB>(sd, layer, jj, v);
       block_reduce(v, s_red);
       if (threadIdx.x == 0) {
         for (int k = 0; k < kPartVals; ++k) sd.partials[(size_t)lt * kPartVals + k] = v[k];
@@ -481,7 +558,10 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
   __threadfence();
   for (int c = lane; c < nchains; c += 32) {
     ChainState st = ea.state[c];
-    if (!st.active) continue;
+    if (!st.active) {
+      if (st.prev_stage != -1) ea.state[c].prev_stage = -1;  // nothing ran: no halo refresh
+      continue;
+    }
     if (st.stage == kStageMeasure) st.n_meas += 1;
     advance_stage(ea.desc[c], st);
     ea.state[c] = st;
@@ -609,6 +689,126 @@ __global__ void k_convert(ChainDesc *desc_dev, double *canon, int to_canonical) 
   }
 }
 
+// ------------------------------------------------------------------ sublattice boxes
+// The paper's boundary exchange (Sec. 2.4: faces, and corners when two or
+// more directions are divided) restated as device copies: every halo site
+// of every box takes its links from the interior site that owns it in the
+// undivided lattice (periodic wrap; a wrap across a glued boundary of the
+// double-layered torus lands in the other layer).  Halo sites are never
+// sources, so the copies do not race.
+
+// Undivided coordinates of a padded-box site; returns false for interior
+// sites.  Sets the owner's virtual layer, padded index and the colour.
+__device__ __forceinline__ bool halo_owner(const ChainDesc &d, int vl, int sp, int &vsrc, int &spsrc, int &colour) {
+  int r = sp, xp[kMaxD];
+  bool halo = false;
+#pragma unroll
+  for (int k = 0; k < kMaxD; ++k) {
+    xp[k] = 0;
+    if (k < d.D) {
+      xp[k] = r % d.dims[k];
+      r /= d.dims[k];
+      if (d.hpad[k] && (xp[k] == 0 || xp[k] == d.dims[k] - 1)) halo = true;
+    }
+  }
+  if (!halo) return false;
+  const int L = vl / d.nb;
+  int b = vl - L * d.nb, flip = 0, bsrc = 0, bmul = 1, par = 0;
+  spsrc = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxD; ++k)
+    if (k < d.D) {
+      const int bc = b % d.bdiv[k];
+      b /= d.bdiv[k];
+      const int n = d.idims[k] * d.bdiv[k];
+      const int glued = d.nlayers == 2 ? ((d.glue_mask >> k) & 1) : 0;
+      int gx = bc * d.idims[k] + xp[k] - d.hpad[k];
+      if (gx < 0) {
+        gx += n;
+        flip ^= glued;
+      } else if (gx >= n) {
+        gx -= n;
+        flip ^= glued;
+      }
+      par += gx;
+      const int bo = gx / d.idims[k];
+      bsrc += bo * bmul;
+      bmul *= d.bdiv[k];
+      spsrc += (gx - bo * d.idims[k] + d.hpad[k]) * d.stride[k];
+    }
+  vsrc = (L ^ flip) * d.nb + bsrc;
+  colour = par & 1;
+  return true;
+}
+
+// Refresh the halos of a divided chain: all links (all = 1, after a start,
+// set_links or re-unitarisation) or, after an update tick, only the
+// (colour, direction) that the tick changed.
+template <class S>
+__global__ void k_halo(const ChainDesc *desc_dev, const ChainState *state_dev, int all) {
+  const ChainDesc &d = *desc_dev;
+  int c0 = 0, c1 = 2, m0 = 0, m1 = d.D;
+  if (!all) {
+    const int ps = state_dev->prev_stage;
+    if (ps >= 0 && ps < 2 * d.D) {
+      c0 = ps / d.D;
+      c1 = c0 + 1;
+      m0 = ps - c0 * d.D;
+      m1 = m0 + 1;
+    } else if (ps != kStageReunit) {
+      return;  // a measurement, or nothing ran: no link changed
+    }
+  }
+  const int Vpad = 2 * d.Vh;
+  const long long n = (long long)d.nlayers * d.nb * Vpad;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int vl = (int)(i / Vpad), sp = (int)(i - (long long)vl * Vpad);
+    int vsrc, spsrc, colour;
+    if (!halo_owner(d, vl, sp, vsrc, spsrc, colour) || colour < c0 || colour >= c1) continue;
+    for (int mu = m0; mu < m1; ++mu) {
+      typename S::Vec *dst = plane_ptr<S>(d, vl, colour, mu) + (sp >> 1);
+      const typename S::Vec *src = plane_ptr<S>(d, vsrc, colour, mu) + (spsrc >> 1);
+#pragma unroll
+      for (int q = 0; q < S::NQ; ++q) dst[(size_t)q * d.Vh] = src[(size_t)q * d.Vh];
+    }
+  }
+}
+
+// Copy links between the undivided layout (plain) and the sublattice boxes
+// (sub): to_sub = 1 scatters into the box interiors, 0 gathers from them.
+template <class S>
+__global__ void k_sub_copy(const ChainDesc *sub_dev, const ChainDesc *plain_dev, int to_sub) {
+  const ChainDesc &d = *sub_dev;
+  const ChainDesc &p = *plain_dev;
+  const size_t nlinks = (size_t)p.nlayers * p.V * p.D;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nlinks; i += (size_t)gridDim.x * blockDim.x) {
+    const int mu = (int)(i % p.D);
+    const size_t ls = i / p.D;
+    const int s = (int)(ls % p.V);
+    const int L = (int)(ls / p.V);
+    int r = s, par = 0, b = 0, bmul = 1, sp = 0;
+    for (int k = 0; k < p.D; ++k) {
+      const int gx = r % p.dims[k];
+      r /= p.dims[k];
+      par += gx;
+      const int bo = gx / d.idims[k];
+      b += bo * bmul;
+      bmul *= d.bdiv[k];
+      sp += (gx - bo * d.idims[k] + d.hpad[k]) * d.stride[k];
+    }
+    const int colour = par & 1;
+    typename S::Vec *pv = plane_ptr<S>(p, L, colour, mu) + (s >> 1);
+    typename S::Vec *sv = plane_ptr<S>(d, L * d.nb + b, colour, mu) + (sp >> 1);
+#pragma unroll
+    for (int q = 0; q < S::NQ; ++q) {
+      if (to_sub)
+        sv[(size_t)q * d.Vh] = pv[(size_t)q * p.Vh];
+      else
+        pv[(size_t)q * p.Vh] = sv[(size_t)q * d.Vh];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ measurement without allocation
 // For callers that cannot allocate device memory (see su3_measure_noalloc):
 // the per-tile partial sums go to a fixed array in the library's own device
@@ -679,22 +879,26 @@ cudaError_t launch_measure_noalloc(int storage, const ChainDesc &d, int block, d
 
 int tick_variants(int storage) { return storage == 0 ? 1 : 5; }
 
-template <int V, bool WT>
+template <int V, bool WT, bool SUB = false>
 static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_t st) {
   if constexpr (V == 10)
-    k_tick<StoreF64x18, 10, WT><<<grid, block, 0, st>>>(ea);
+    k_tick<StoreF64x18, 10, WT, SUB><<<grid, block, 0, st>>>(ea);
   else
-    k_tick<StoreF32x12, V, WT><<<grid, block, 0, st>>>(ea);
+    k_tick<StoreF32x12, V, WT, SUB><<<grid, block, 0, st>>>(ea);
   return cudaGetLastError();
 }
 
-template <int V, bool WT>
+template <int V, bool WT, bool SUB = false>
 static cudaError_t occ_v(int block, int *ctas) {
   if constexpr (V == 10)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF64x18, 10, WT>, block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF64x18, 10, WT, SUB>, block, 0);
   else
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF32x12, V, WT>, block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF32x12, V, WT, SUB>, block, 0);
 }
+
+// A chain divided into sublattice boxes runs one kernel form: FP32 the
+// rolled 128-register variant (3), FP64 its only one.
+constexpr int kSubVariant = 3;
 
 int tick_max_threads(int storage, int variant) {
   if (storage == 0) return TickBounds<10>::kThreads;
@@ -708,8 +912,9 @@ int tick_max_threads(int storage, int variant) {
 }
 
 template <bool WT>
-static cudaError_t launch_tick_w(int storage, int variant, const EngineArgs &ea, int grid, int block,
+static cudaError_t launch_tick_w(int storage, int variant, bool sub, const EngineArgs &ea, int grid, int block,
                                  cudaStream_t st) {
+  if (sub) return storage == 0 ? tick_v<10, WT, true>(ea, grid, block, st) : tick_v<kSubVariant, WT, true>(ea, grid, block, st);
   if (storage == 0) return tick_v<10, WT>(ea, grid, block, st);
   switch (variant) {
     case 0: return tick_v<0, WT>(ea, grid, block, st);
@@ -720,11 +925,35 @@ static cudaError_t launch_tick_w(int storage, int variant, const EngineArgs &ea,
   }
 }
 
-cudaError_t launch_tick(int storage, int variant, bool weighted, const EngineArgs &ea, int grid, int block,
+cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, const EngineArgs &ea, int grid, int block,
                         cudaStream_t st) {
+  if (sub) variant = storage == 0 ? 0 : kSubVariant;
   if (block > tick_max_threads(storage, variant)) return cudaErrorInvalidConfiguration;
-  return weighted ? launch_tick_w<true>(storage, variant, ea, grid, block, st)
-                  : launch_tick_w<false>(storage, variant, ea, grid, block, st);
+  return weighted ? launch_tick_w<true>(storage, variant, sub, ea, grid, block, st)
+                  : launch_tick_w<false>(storage, variant, sub, ea, grid, block, st);
+}
+
+cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, int all,
+                        long long padded_sites, cudaStream_t st) {
+  const int block = 256;
+  const long long want = (padded_sites + block - 1) / block;
+  const int grid = (int)(want < 16384 ? (want > 0 ? want : 1) : 16384);
+  if (storage == 0)
+    k_halo<StoreF64x18><<<grid, block, 0, st>>>(desc_dev, state_dev, all);
+  else
+    k_halo<StoreF32x12><<<grid, block, 0, st>>>(desc_dev, state_dev, all);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub_copy(int storage, const ChainDesc *sub_dev, const ChainDesc *plain_dev, size_t nlinks,
+                            int to_sub, cudaStream_t st) {
+  const int block = 256;
+  const int grid = (int)((nlinks + block - 1) / block < 65536 ? (nlinks + block - 1) / block : 65536);
+  if (storage == 0)
+    k_sub_copy<StoreF64x18><<<grid, block, 0, st>>>(sub_dev, plain_dev, to_sub);
+  else
+    k_sub_copy<StoreF32x12><<<grid, block, 0, st>>>(sub_dev, plain_dev, to_sub);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st) {
@@ -759,7 +988,8 @@ cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, doub
 }
 
 template <bool WT>
-static cudaError_t tick_occupancy_w(int storage, int variant, int block, int *ctas_per_sm) {
+static cudaError_t tick_occupancy_w(int storage, int variant, bool sub, int block, int *ctas_per_sm) {
+  if (sub) return storage == 0 ? occ_v<10, WT, true>(block, ctas_per_sm) : occ_v<kSubVariant, WT, true>(block, ctas_per_sm);
   if (storage == 0) return occ_v<10, WT>(block, ctas_per_sm);
   switch (variant) {
     case 0: return occ_v<0, WT>(block, ctas_per_sm);
@@ -770,11 +1000,12 @@ static cudaError_t tick_occupancy_w(int storage, int variant, int block, int *ct
   }
 }
 
-cudaError_t tick_occupancy(int storage, int variant, bool weighted, int block, int *ctas_per_sm) {
+cudaError_t tick_occupancy(int storage, int variant, bool weighted, bool sub, int block, int *ctas_per_sm) {
   *ctas_per_sm = 0;
+  if (sub) variant = storage == 0 ? 0 : kSubVariant;
   if (block > tick_max_threads(storage, variant)) return cudaSuccess;
-  return weighted ? tick_occupancy_w<true>(storage, variant, block, ctas_per_sm)
-                  : tick_occupancy_w<false>(storage, variant, block, ctas_per_sm);
+  return weighted ? tick_occupancy_w<true>(storage, variant, sub, block, ctas_per_sm)
+                  : tick_occupancy_w<false>(storage, variant, sub, block, ctas_per_sm);
 }
 
 void host_advance_stage(const ChainDesc &d, ChainState &s) { advance_stage(d, s); }

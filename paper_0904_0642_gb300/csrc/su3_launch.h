@@ -11,16 +11,23 @@ namespace su3g {
 // 2 = 96, 3 = 128, 4 = 85 registers with a rolled staple loop; FP64: one);
 // a variant limits the CTA width to tick_max_threads.  weighted selects the
 // form compiled for two-coupling DLT chains (needed when any chain of the
-// launch has beta1 != beta).
+// launch has beta1 != beta); sub the form for a chain divided into
+// sublattice boxes (it fixes the variant: 3 for FP32).
 int tick_variants(int storage);
 int tick_max_threads(int storage, int variant);
-cudaError_t launch_tick(int storage, int variant, bool weighted, const EngineArgs &ea, int grid, int block,
+cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, const EngineArgs &ea, int grid, int block,
                         cudaStream_t st);
+// Halo refresh of a divided chain (after its tick, or all links), and the
+// copies between its sublattice boxes and the undivided layout.
+cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, int all,
+                        long long padded_sites, cudaStream_t st);
+cudaError_t launch_sub_copy(int storage, const ChainDesc *sub_dev, const ChainDesc *plain_dev, size_t nlinks,
+                            int to_sub, cudaStream_t st);
 cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st);
 cudaError_t launch_start(int storage, ChainDesc *desc_dev, size_t nlinks, int hot, cudaStream_t st);
 cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, double *canon, int to_canonical,
                            cudaStream_t st);
-cudaError_t tick_occupancy(int storage, int variant, bool weighted, int block, int *ctas_per_sm);
+cudaError_t tick_occupancy(int storage, int variant, bool weighted, bool sub, int block, int *ctas_per_sm);
 void host_advance_stage(const ChainDesc &d, ChainState &s);
 // Fixed-order sum of n booked action-change slots into *out (device).
 cudaError_t launch_action_sum(const double *slots, int n, double *out, cudaStream_t st);

@@ -80,3 +80,49 @@ def test_null_handles_are_errors():
     assert L.su3_ensemble_sweep(None, 1) == su3.SU3_EINVAL
     assert L.su3_server_poll(None, 1, None) == su3.SU3_EINVAL
     assert "NULL" in su3.su3_last_error()
+
+
+@pytest.mark.parametrize("dims,ndiv,ok", [
+    ([8, 8, 8, 8], [2, 2, 1, 1], True),
+    ([8, 8, 8, 8], [2, 2, 2, 2], True),
+    ([12, 12, 4, 4], [3, 3, 1, 1], True),    # the paper's (mpifactor, ndmpi) = (3, 2) on 4^4 sublattices
+    ([8, 8, 8, 8], [0, 1, 0, 1], True),      # 0 and 1 both mean undivided
+    ([8, 8, 8, 8], [4, 1, 1, 1], True),      # sublattice extent 2
+    ([6, 8, 8, 8], [3, 1, 1, 1], True),      # sublattice extent 2
+    ([8, 8, 8, 8], [3, 1, 1, 1], False),     # 3 does not divide 8
+    ([6, 8, 8, 8], [2, 1, 1, 1], False),     # sublattice extent 3 is odd
+    ([8, 8, 8], [1, 1, 1, 2], False),        # a direction beyond D
+    ([8, 8, 8, 8], [-1, 1, 1, 1], False),
+])
+def test_sublattice_validation(dims, ndiv, ok):
+    """Sec. 2.4: sublattices of even extent (the checkerboard needs it)
+    that divide the lattice exactly."""
+    c = su3.make_config(dims, storage=su3.SU3_FP32_12, ndiv=ndiv)
+    nbytes = su3.su3_link_bytes(c)
+    if not ok:
+        assert nbytes == 0
+        assert "ndiv" in su3.su3_last_error()
+        return
+    plain = su3.su3_link_bytes(su3.make_config(dims, storage=su3.SU3_FP32_12))
+    if max(ndiv) <= 1:
+        assert nbytes == plain
+        return
+    # boxes: every sublattice padded by one halo layer per side of each cut direction
+    V = 1
+    nb = 1
+    for n, k in zip(dims, ndiv):
+        k = max(k, 1)
+        nb *= k
+        V *= n // k + (2 if k > 1 else 0)
+    assert nbytes == plain + len(dims) * nb * V * 48
+
+
+def test_sublattice_rejections():
+    # a caller-owned buffer, and two couplings on a DLT cut along a glued direction
+    c = su3.make_config([8, 8, 8, 8], storage=su3.SU3_FP32_12, ndiv=[2, 1, 1, 1], buffer=(1 << 20, 1 << 30))
+    assert su3.su3_link_bytes(c) == 0 and "link_buffer" in su3.su3_last_error()
+    c = su3.make_config([8, 8, 8, 8], boundary=su3.SU3_DLT, beta1=5.0, storage=su3.SU3_FP32_12, ndiv=[2, 1, 1, 1])
+    assert su3.su3_link_bytes(c) == 0 and "two couplings" in su3.su3_last_error()
+    c = su3.make_config([8, 8, 8, 8], boundary=su3.SU3_DLT, glue_mask=0b1000, beta1=5.0, storage=su3.SU3_FP32_12,
+                        ndiv=[2, 1, 1, 1])
+    assert su3.su3_link_bytes(c) > 0  # direction 0 is not glued
