@@ -382,8 +382,8 @@ class Lattice:
     def polyakov(self, layer=-1):
         return su3_polyakov(self.h, layer)
 
-    def measurements(self):
-        return su3_measurements(self.h, self.nlayers)
+    def measurements(self, max_entries=1 << 16):
+        return su3_measurements(self.h, self.nlayers, max_entries)
 
     def get_links(self) -> np.ndarray:
         out = np.zeros((self.nlayers, self.V, self.D, 3, 3, 2), dtype=np.float64)

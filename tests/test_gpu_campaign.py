@@ -1,0 +1,42 @@
+"""The paper's verification campaign (Sec. 3: eq. act1, Tables 1-3) at a
+sixteenth of its statistics: binned error bars (32 bins), tau_int, and
+Gaussian difference tests against every printed reference value and, for
+the divided-lattice rows, against the row above (as the tables do).  Seeds
+are fixed, so the outcome is reproducible."""
+import numpy as np
+import pytest
+
+from paper_0904_0642_gb300 import campaign
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+Q_MIN = 1e-4  # about 3.9 standard deviations
+
+
+@pytest.fixture(scope="module")
+def result():
+    return campaign.run(scale=1 / 16, log=lambda *_: None)
+
+
+def test_every_gaussian_difference_test_passes(result):
+    qs = {(r["run"], r["observable"], str(r["np"]), k): q for r in result["rows"] for k, q in r["q"].items()}
+    assert len(qs) == 2 + 1 + 4 + 1 + 2 * 6
+    bad = {k: q for k, q in qs.items() if q < Q_MIN}
+    assert not bad, bad
+    # the Q values of correct estimates scatter over (0, 1]
+    assert 0.15 < np.mean(list(qs.values())) < 0.85
+
+
+def test_bins_are_longer_than_the_autocorrelation(result):
+    """The paper's criterion for 32 bins (Sec. 3.1.1): a bin of nmeas
+    measurements must be long compared with tau_int (at this sixteenth of
+    the statistics a bin is 256 measurements; tau_int of the 4^4 run at
+    beta = 5.6 is ~25, of the others 10-30)."""
+    for r in result["rows"]:
+        assert r["tau_int"] * 5 < result["nmeas"], (r["run"], r["np"], r["tau_int"])
+        assert np.isfinite(r["err"]) and r["err"] > 0
+
+
+def test_divided_rows_ran(result):
+    nps = sorted(r["np"] for r in result["rows"] if r["np"] != "-")
+    assert nps == [2, 4, 4, 8, 8, 16]
