@@ -494,23 +494,60 @@ __device__ __forceinline__ void rotate_rows(M3<R> &m, int i, int j, R r0, R r1, 
   }
 }
 
+// The quaternion projection a of the (i, j) block of W = U A, taken from
+// the current (already rotated) U and the staple sum A: four sums of six
+// products each.  a0 = Re(w_ii + w_jj)/2, a1 = Im(w_ij + w_ji)/2,
+// a2 = Re(w_ij - w_ji)/2, a3 = Im(w_ii - w_jj)/2 with w_ab = sum_k U_ak A_kb.
+template <typename R>
+__device__ __forceinline__ void block_projection(const M3<R> &U, const M3<R> &A, int i, int j, R &a0, R &a1, R &a2,
+                                                 R &a3) {
+  R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const C<R> ui = U.e[i][k], uj = U.e[j][k], ai = A.e[k][i], aj = A.e[k][j];
+    // Re(u_ik a_ki + u_jk a_kj)
+    s0 = fm(ui.re, ai.re, s0);
+    s0 = fm(-ui.im, ai.im, s0);
+    s0 = fm(uj.re, aj.re, s0);
+    s0 = fm(-uj.im, aj.im, s0);
+    // Im(u_ik a_kj + u_jk a_ki)
+    s1 = fm(ui.re, aj.im, s1);
+    s1 = fm(ui.im, aj.re, s1);
+    s1 = fm(uj.re, ai.im, s1);
+    s1 = fm(uj.im, ai.re, s1);
+    // Re(u_ik a_kj - u_jk a_ki)
+    s2 = fm(ui.re, aj.re, s2);
+    s2 = fm(-ui.im, aj.im, s2);
+    s2 = fm(-uj.re, ai.re, s2);
+    s2 = fm(uj.im, ai.im, s2);
+    // Im(u_ik a_ki - u_jk a_kj)
+    s3 = fm(ui.re, ai.im, s3);
+    s3 = fm(ui.im, ai.re, s3);
+    s3 = fm(-uj.re, aj.im, s3);
+    s3 = fm(-uj.im, aj.re, s3);
+  }
+  a0 = R(0.5) * s0;
+  a1 = R(0.5) * s1;
+  a2 = R(0.5) * s2;
+  a3 = R(0.5) * s3;
+}
+
 // dretr (out): the change of Re Tr(U A) = Re Tr W.  An accepted subgroup
 // replaces Re(w_ii + w_jj) = 2 a0 = 2 k v0 by 2 k x0 and leaves the third
 // diagonal element alone, so the change is the sum of 2 (k x0 - a0).
+// W itself is never formed: each subgroup projects the block of the current
+// U times A (block_projection), which equals the block of the rotated W.
 template <typename R>
 __device__ __forceinline__ void cm_update(M3<R> &U, const M3<R> &A, R beta, int hits, uint2 key, uint32_t c0,
                                           uint32_t c1, int colour, int mu, uint32_t &nprop, uint32_t &nacc,
                                           R &dretr) {
-  M3<R> W = mul_nn(U, A);
   dretr = R(0);
 #pragma unroll
   for (int sg = 0; sg < 3; ++sg) {
     const int i = (sg == 2) ? 1 : 0;
     const int j = (sg == 0) ? 1 : 2;
-    const R a0 = R(0.5) * (W.e[i][i].re + W.e[j][j].re);
-    const R a1 = R(0.5) * (W.e[i][j].im + W.e[j][i].im);
-    const R a2 = R(0.5) * (W.e[i][j].re - W.e[j][i].re);
-    const R a3 = R(0.5) * (W.e[i][i].im - W.e[j][j].im);
+    R a0, a1, a2, a3;
+    block_projection(U, A, i, j, a0, a1, a2, a3);
     const R k = sqrt(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3);
     if (!(k > (sizeof(R) == 4 ? R(1e-30) : R(1e-300)))) continue;
     const R alpha = R(2) * beta * k / R(3);
@@ -526,7 +563,6 @@ __device__ __forceinline__ void cm_update(M3<R> &U, const M3<R> &A, R beta, int 
     const R r2 = -x[0] * v2 + v0 * x[2] + (x[3] * v1 - x[1] * v3);
     const R r3 = -x[0] * v3 + v0 * x[3] + (x[1] * v2 - x[2] * v1);
     rotate_rows(U, i, j, r0, r1, r2, r3);
-    if (sg < 2) rotate_rows(W, i, j, r0, r1, r2, r3);
   }
 }
 
