@@ -432,25 +432,50 @@ def main():
                             "reunit_us": 1e3 * prof["reunit_ms"] / max(1, prof["reunit_launches"]),
                             "measure_us": 1e3 * prof["measure_ms"] / max(1, prof["measure_launches"])}
 
-        # End to end through the C ABI: each step uploads the step's input
-        # configuration from pinned host memory (canonical FP64 layout),
-        # runs the 10 sweeps + re-unitarisation, and reads the plaquette and
-        # Polyakov loop back to the host.
-        host_in = torch.empty((links * 18,), dtype=torch.float64, pin_memory=True).numpy()
-        host_in[:] = lat.get_links().reshape(-1)
+        # End to end through the C ABI: every step uploads that step's input
+        # configuration from pinned host memory (su3_stage_links_ex on the
+        # library's copy stream: the upload of step k+1 runs while step k
+        # sweeps), applies it (su3_apply_links), runs the 10 sweeps +
+        # re-unitarisation + measurement, and reads that step's plaquette
+        # and Polyakov loop back (su3_measurement_latest, 80 bytes).  The
+        # input is the two-row FP32 form of the configuration (12 floats per
+        # link, the storage format of this workload); the canonical FP64
+        # layout (18 doubles per link) is timed the same way beside it.
+        canon = lat.get_links()
         k_e2e = max(3, args.steps // 10)
-        lat.sweep(SWEEPS_PER_STEP)  # warm
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(k_e2e):
-            lat.set_links(host_in)
-            lat.sweep(SWEEPS_PER_STEP)
-            lat.plaquette()
-            lat.polyakov()
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
-        line["e2e"] = {"value": world * k_e2e * SWEEPS_PER_STEP * links / t_e2e, "unit": UNIT,
-                       "h2d_bytes_per_step": links * 18 * 8, "d2h_bytes_per_step": 2 * 3 * 5 * 8,
-                       "steps": k_e2e}
+
+        def e2e_run(fmt):
+            if fmt == su3.SU3_LINKS_FP32_12:
+                host = torch.empty((links * 12,), dtype=torch.float32, pin_memory=True).numpy()
+                host[:] = canon[..., :2, :, :].reshape(-1)
+            else:
+                host = torch.empty((links * 18,), dtype=torch.float64, pin_memory=True).numpy()
+                host[:] = canon.reshape(-1)
+            lat.sweep(SWEEPS_PER_STEP)  # warm
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat.stage_links(host, fmt=fmt)
+            for k in range(k_e2e):
+                lat.apply_links()
+                lat.sweep(SWEEPS_PER_STEP)
+                if k + 1 < k_e2e:
+                    lat.stage_links(host, fmt=fmt)
+                result = lat.latest_measurement()
+            t = max_over_ranks(time.perf_counter() - t0)
+            # one upload alone (copy + apply + a synchronising read), for its bandwidth
+            torch.cuda.synchronize()
+            u0 = time.perf_counter()
+            lat.stage_links(host, fmt=fmt)
+            lat.apply_links()
+            lat.stats()  # synchronises
+            upload_s = time.perf_counter() - u0
+            return {"value": world * k_e2e * SWEEPS_PER_STEP * links / t, "unit": UNIT,
+                    "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(result.size) * 8,
+                    "steps": k_e2e, "upload_apply_ms": 1e3 * upload_s}
+
+        line["e2e"] = e2e_run(su3.SU3_LINKS_FP32_12)
+        line["e2e"]["input"] = "pinned host, rows 1-2 of every link as FP32 (12 floats), copy stream overlapping the previous step"
+        line["e2e_fp64_canonical_input"] = e2e_run(su3.SU3_LINKS_FP64_18)
 
         # Plain FP64 single chain, 18-real storage, same workload and seed.
         lat64 = su3.Lattice(DIMS, beta=BETA, seed=SEED + rank, hits=HITS, storage=su3.SU3_FP64_18,

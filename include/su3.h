@@ -162,11 +162,41 @@ su3_status su3_measure_async(su3_lattice *lat, double *device_out);
  * host buffer; *count receives the number copied.  Synchronises. */
 su3_status su3_measurements(su3_lattice *lat, double *host_out, size_t max, size_t *count);
 
+/* The most recent of those recorded measurements only: 5*(layers+1)
+ * doubles (n must hold them).  ENOTFOUND when none was recorded yet.
+ * Synchronises. */
+su3_status su3_measurement_latest(su3_lattice *lat, double *host_out, size_t n);
+
 /* Copy all links to / from the host in the canonical layout; n is the
  * number of doubles in the host buffer (>= 18 * links).  set_links rounds
  * to the storage precision (FP32_12 keeps rows 1 and 2).  Synchronous. */
 su3_status su3_get_links(su3_lattice *lat, double *host, size_t n);
 su3_status su3_set_links(su3_lattice *lat, const double *host, size_t n);
+
+/* Asynchronous link input, for inputs that arrive while the lattice is
+ * sweeping.  su3_stage_links starts the copy of n >= links*18 doubles
+ * (canonical layout, as su3_set_links) from host memory into one of two
+ * device staging buffers on the library's own copy stream and returns at
+ * once; with pinned host memory the copy overlaps the sweeps already
+ * queued.  At most one staged input may wait: EBUSY until su3_apply_links.
+ * su3_apply_links makes the lattice's stream wait for that copy, then
+ * converts the staged links into the lattice (divided lattices: scatter and
+ * halo refresh) and restarts the action bookkeeping, all queued on the
+ * stream without blocking the host; EINVAL when nothing is staged.  The
+ * host buffer is read asynchronously: keep it unchanged until a
+ * synchronising call on the lattice (su3_plaquette, su3_get_links, ...)
+ * has returned after the matching su3_apply_links. */
+su3_status su3_stage_links(su3_lattice *lat, const double *host, size_t n);
+su3_status su3_apply_links(su3_lattice *lat);
+
+/* su3_stage_links with a choice of host format: SU3_LINKS_FP64_18 (as
+ * su3_stage_links: n >= links*18 doubles) or SU3_LINKS_FP32_12 (rows 1 and
+ * 2 of every link as floats, [layer][i_s-1][mu][row 1..2][col][re,im], so
+ * n >= links*12 floats, 16-byte aligned; row 3 is rebuilt as
+ * conj(row1 x row2) -- the two-row form of the FP32_12 storage, a third of
+ * the bytes of the canonical layout). */
+typedef enum { SU3_LINKS_FP64_18 = 0, SU3_LINKS_FP32_12 = 1 } su3_links_format;
+su3_status su3_stage_links_ex(su3_lattice *lat, const void *host, size_t n, int format);
 
 /* Counters: FHKP proposals and accepted proposals since creation, and the
  * number of completed sweeps (the sweep counter of the random numbers). */

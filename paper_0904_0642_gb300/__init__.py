@@ -30,11 +30,12 @@ SU3_OK, SU3_EINVAL, SU3_ENOMEM, SU3_ECUDA, SU3_ETIMEOUT, SU3_EBUSY, SU3_ENOTFOUN
 SU3_PBC, SU3_DLT = 0, 1
 SU3_FP64_18, SU3_FP32_12 = 0, 1
 SU3_START_COLD, SU3_START_HOT = 0, 1
+SU3_LINKS_FP64_18, SU3_LINKS_FP32_12 = 0, 1
 
 EXPORTED = [
     "su3_config_init", "su3_link_bytes", "su3_lattice_create", "su3_lattice_create_ex", "su3_lattice_destroy",
     "su3_sweep", "su3_reunitarize", "su3_plaquette", "su3_polyakov", "su3_measure_async", "su3_measurements",
-    "su3_get_links", "su3_set_links", "su3_stats", "su3_action", "su3_action_reset", "su3_set_sweep_counter", "su3_lattice_info", "su3_set_launch",
+    "su3_get_links", "su3_set_links", "su3_stage_links", "su3_stage_links_ex", "su3_apply_links", "su3_measurement_latest", "su3_stats", "su3_action", "su3_action_reset", "su3_set_sweep_counter", "su3_lattice_info", "su3_set_launch",
     "su3_autotune", "su3_use_graph", "su3_set_profiling", "su3_get_profile", "su3_ensemble_create", "su3_ensemble_destroy", "su3_ensemble_sweep",
     "su3_ensemble_measure", "su3_ensemble_get_links", "su3_ensemble_measurements", "su3_ensemble_set_launch", "su3_ensemble_autotune", "su3_ensemble_use_graph",
     "su3_ensemble_set_profiling", "su3_ensemble_get_profile",
@@ -105,6 +106,10 @@ def lib():
             "su3_measurements": (c_int, [vp, dp, sz, POINTER(sz)]),
             "su3_get_links": (c_int, [vp, dp, sz]),
             "su3_set_links": (c_int, [vp, dp, sz]),
+            "su3_stage_links": (c_int, [vp, dp, sz]),
+            "su3_stage_links_ex": (c_int, [vp, c_void_p, sz, c_int]),
+            "su3_measurement_latest": (c_int, [vp, dp, sz]),
+            "su3_apply_links": (c_int, [vp]),
             "su3_stats": (c_int, [vp, u64p, u64p, u64p]),
             "su3_set_sweep_counter": (c_int, [vp, c_uint64]),
             "su3_action": (c_int, [vp, dp, dp]),
@@ -231,6 +236,27 @@ def su3_get_links(h, out: np.ndarray):
 def su3_set_links(h, links: np.ndarray):
     links = np.ascontiguousarray(links, dtype=np.float64)
     _check(lib().su3_set_links(h, _dp(links), links.size))
+
+
+def su3_stage_links(h, links: np.ndarray):
+    """Start the asynchronous copy of links (contiguous float64, canonical
+    layout); the caller keeps `links` alive and unchanged until a
+    synchronising call after su3_apply_links."""
+    _check(lib().su3_stage_links(h, _dp(links), links.size))
+
+
+def su3_apply_links(h):
+    _check(lib().su3_apply_links(h))
+
+
+def su3_stage_links_ex(h, links: np.ndarray, fmt: int):
+    _check(lib().su3_stage_links_ex(h, links.ctypes.data, links.size, fmt))
+
+
+def su3_measurement_latest(h, nlayers: int) -> np.ndarray:
+    out = np.zeros(5 * (nlayers + 1), dtype=np.float64)
+    _check(lib().su3_measurement_latest(h, _dp(out), out.size))
+    return out.reshape(nlayers + 1, 5)
 
 
 def su3_stats(h):
@@ -392,6 +418,29 @@ class Lattice:
 
     def set_links(self, links: np.ndarray):
         su3_set_links(self.h, links)
+
+    def stage_links(self, links: np.ndarray, fmt=SU3_LINKS_FP64_18):
+        """Queue links for su3_apply_links: canonical float64 (fmt
+        SU3_LINKS_FP64_18) or rows 1, 2 as float32 (SU3_LINKS_FP32_12, 12 per
+        link); the copy runs while earlier sweeps run.  Pinned host memory
+        makes it asynchronous."""
+        dt = np.float64 if fmt == SU3_LINKS_FP64_18 else np.float32
+        links = np.ascontiguousarray(links, dtype=dt)
+        su3_stage_links_ex(self.h, links, fmt)
+        self._staged = (getattr(self, "_staged", (None, None))[1], links)  # alive until copied
+
+    def latest_measurement(self) -> np.ndarray:
+        """The last measurement recorded by measure_every: [layer.., all] x
+        (total, space, time, poly_re, poly_im)."""
+        return su3_measurement_latest(self.h, self.nlayers)
+
+    def apply_links(self):
+        su3_apply_links(self.h)
+
+    def measure_into(self, device_ptr: int):
+        """Plaquette and Polyakov values of every layer and of the whole
+        lattice into device memory (5 * (nlayers + 1) doubles), queued."""
+        su3_measure_async(self.h, device_ptr)
 
     def stats(self):
         return su3_stats(self.h)

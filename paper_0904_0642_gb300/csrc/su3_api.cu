@@ -181,7 +181,7 @@ struct Chain {
   unsigned long long *counters = nullptr;
   double *action_slots = nullptr;  // booked action changes, one slot per warp of sites
   int n_action_slots = 0;
-  double action_ref = 0.0;         // action at the last reset (su3_action)
+  double *ref_meas = nullptr;      // device: the measurement taken at the last bookkeeping reset
   size_t link_bytes = 0;
   size_t bytes_total = 0;  // device bytes held (links if owned + scratch)
   uint64_t job_id = 0;     // server only
@@ -418,6 +418,8 @@ struct Engine {
     cudaFree(ch.counters);
     cudaFree(ch.action_slots);
     ch.action_slots = nullptr;
+    cudaFree(ch.ref_meas);
+    ch.ref_meas = nullptr;
     ch.links = nullptr;
     ch.results = ch.partials = nullptr;
     ch.counters = nullptr;
@@ -494,6 +496,11 @@ struct Engine {
     }
     CU(cudaMemsetAsync(ch.action_slots, 0, (size_t)ch.n_action_slots * sizeof(double), stream));
     ch.bytes_total += (size_t)ch.n_action_slots * sizeof(double);
+    if (cudaMalloc(&ch.ref_meas, 3 * kMeasVals * sizeof(double)) != cudaSuccess) {
+      free_chain(ch);
+      return fail(SU3_ENOMEM, "action reference allocation failed");
+    }
+    CU(cudaMemsetAsync(ch.ref_meas, 0, 3 * kMeasVals * sizeof(double), stream));
     CU(cudaMemsetAsync(ch.counters, 0, 2 * sizeof(unsigned long long), stream));
     CU(cudaMemsetAsync(ch.results, 0, nres * sizeof(double), stream));
     fill_desc(ch, block);
@@ -833,13 +840,36 @@ struct Engine {
     return SU3_OK;
   }
 
+  // The bookkeeping restarts from the current links: clear the booked
+  // changes and measure the reference action on the device, in stream
+  // order and without waiting (su3_action reads the reference).
   su3_status action_reset(size_t c) {
     Chain &ch = chains[c];
-    double S = 0.0;
-    TRY(direct_action(c, &S));
-    ch.action_ref = std::isnan(S) ? 0.0 : S;
     CU(cudaMemsetAsync(ch.action_slots, 0, (size_t)ch.n_action_slots * sizeof(double), stream));
+    if (!ch.desc.weighted) {
+      ChainDesc *dd = nullptr;
+      TRY(io_desc(c, &dd));
+      const ChainDesc &md = ch.sub ? ch.pdesc : ch.desc;
+      CU(launch_measure(storage, dd, md.nlayers * md.tiles_per_layer, block, ch.ref_meas, stream));
+    }
+    return SU3_OK;
+  }
+
+  // Action at the last reset (0 for the two-coupling DLT: its booked value
+  // is the change since the reset).  Synchronises.
+  su3_status action_reference(size_t c, double *S) {
+    Chain &ch = chains[c];
+    if (ch.desc.weighted) {
+      *S = 0.0;
+      return SU3_OK;
+    }
+    const int slot = ch.desc.nlayers * kMeasVals;
+    CU(cudaMemcpyAsync(h_pinned, ch.ref_meas, (slot + kMeasVals) * sizeof(double), cudaMemcpyDeviceToHost, stream));
     CU(cudaStreamSynchronize(stream));
+    double v[3 * kMeasVals];
+    std::memcpy(v, h_pinned, (slot + kMeasVals) * sizeof(double));
+    const double np = (double)ch.desc.nlayers * ch.desc.V * ch.desc.D * (ch.desc.D - 1) / 2;
+    *S = ch.cfg.beta * np * (1.0 - v[slot]);
     return SU3_OK;
   }
 
@@ -874,6 +904,24 @@ struct Engine {
 
 struct su3_lattice {
   Engine eng;
+  // asynchronous link input (su3_stage_links / su3_apply_links): two
+  // device buffers in the canonical layout, filled on a copy stream
+  cudaStream_t copy_stream = nullptr;
+  double *stage[2] = {nullptr, nullptr};
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+  bool used[2] = {false, false};
+  int fmt[2] = {0, 0};  // su3_links_format of the staged copy
+  int next = 0, pending = -1;
+  ~su3_lattice() {
+    if (copy_stream) cudaStreamSynchronize(copy_stream);
+    if (eng.stream) cudaStreamSynchronize(eng.stream);
+    for (int b = 0; b < 2; ++b) {
+      cudaFree(stage[b]);
+      if (copied[b]) cudaEventDestroy(copied[b]);
+      if (consumed[b]) cudaEventDestroy(consumed[b]);
+    }
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+  }
 };
 
 static su3_status make_lattice(const su3_config *cfg, su3_lattice **out) {
@@ -1016,6 +1064,20 @@ extern "C" su3_status su3_measurements(su3_lattice *lat, double *host_out, size_
   return chain_measurements(lat->eng, 0, host_out, max, count);
 }
 
+extern "C" su3_status su3_measurement_latest(su3_lattice *lat, double *host_out, size_t n) {
+  LAT_CHECK(lat);
+  Engine &e = lat->eng;
+  const Chain &ch = e.chains[0];
+  const size_t per = (size_t)(ch.desc.nlayers + 1) * kMeasVals;
+  if (!host_out || n < per) return fail(SU3_EINVAL, "host_out holds %zu doubles, %zu needed", n, per);
+  if (ch.state.n_meas == 0) return fail(SU3_ENOTFOUND, "no measurement recorded yet (measure_every)");
+  const size_t slot = (size_t)((ch.state.n_meas - 1) % (uint32_t)ch.desc.result_cap);
+  CU(cudaMemcpyAsync(e.h_pinned, ch.results + slot * per, per * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  CU(cudaStreamSynchronize(e.stream));
+  std::memcpy(host_out, e.h_pinned, per * sizeof(double));
+  return SU3_OK;
+}
+
 extern "C" su3_status su3_get_links(su3_lattice *lat, double *host, size_t n) {
   LAT_CHECK(lat);
   return lat->eng.get_links(0, host, n);
@@ -1024,6 +1086,61 @@ extern "C" su3_status su3_get_links(su3_lattice *lat, double *host, size_t n) {
 extern "C" su3_status su3_set_links(su3_lattice *lat, const double *host, size_t n) {
   LAT_CHECK(lat);
   return lat->eng.set_links(0, host, n);
+}
+
+extern "C" su3_status su3_stage_links_ex(su3_lattice *lat, const void *host, size_t n, int format) {
+  LAT_CHECK(lat);
+  Engine &e = lat->eng;
+  const Chain &ch = e.chains[0];
+  const size_t nlinks = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
+  if (format != SU3_LINKS_FP64_18 && format != SU3_LINKS_FP32_12) return fail(SU3_EINVAL, "unknown format %d", format);
+  const size_t per = format == SU3_LINKS_FP64_18 ? 18 : 12;
+  const size_t bytes = nlinks * (format == SU3_LINKS_FP64_18 ? 18 * sizeof(double) : 12 * sizeof(float));
+  if (!host || n < nlinks * per) return fail(SU3_EINVAL, "host buffer holds %zu values, %zu needed", n, nlinks * per);
+  if (lat->pending >= 0) return fail(SU3_EBUSY, "staged links not applied yet (su3_apply_links)");
+  if (!lat->copy_stream) {
+    CU(cudaStreamCreateWithFlags(&lat->copy_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      CU(cudaEventCreateWithFlags(&lat->copied[b], cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&lat->consumed[b], cudaEventDisableTiming));
+    }
+  }
+  const int b = lat->next;
+  // sized for the larger format, so that formats may alternate
+  if (!lat->stage[b]) CU(cudaMalloc(&lat->stage[b], nlinks * 18 * sizeof(double)));
+  // the conversion that read this buffer last must be done before it is overwritten
+  if (lat->used[b]) CU(cudaStreamWaitEvent(lat->copy_stream, lat->consumed[b], 0));
+  CU(cudaMemcpyAsync(lat->stage[b], host, bytes, cudaMemcpyHostToDevice, lat->copy_stream));
+  CU(cudaEventRecord(lat->copied[b], lat->copy_stream));
+  lat->fmt[b] = format;
+  lat->pending = b;
+  lat->next = b ^ 1;
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_stage_links(su3_lattice *lat, const double *host, size_t n) {
+  return su3_stage_links_ex(lat, host, n, SU3_LINKS_FP64_18);
+}
+
+extern "C" su3_status su3_apply_links(su3_lattice *lat) {
+  LAT_CHECK(lat);
+  Engine &e = lat->eng;
+  if (lat->pending < 0) return fail(SU3_EINVAL, "no staged links (su3_stage_links)");
+  if (e.tiles_dirty) TRY(e.rebuild());
+  Chain &ch = e.chains[0];
+  const int b = lat->pending;
+  const size_t nlinks = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
+  CU(cudaStreamWaitEvent(e.stream, lat->copied[b], 0));
+  ChainDesc *dd = ch.sub ? ch.d_pdesc : e.d_desc;
+  if (lat->fmt[b] == SU3_LINKS_FP32_12)
+    CU(launch_convert_rows2(e.storage, dd, nlinks, reinterpret_cast<const float *>(lat->stage[b]), e.stream));
+  else
+    CU(launch_convert(e.storage, dd, nlinks, lat->stage[b], 0, e.stream));
+  if (ch.sub) TRY(e.sub_sync(0, 1));
+  CU(cudaEventRecord(lat->consumed[b], e.stream));
+  lat->used[b] = true;
+  lat->pending = -1;
+  return e.action_reset(0);  // the links changed without bookkeeping
 }
 
 extern "C" su3_status su3_stats(su3_lattice *lat, uint64_t *proposals, uint64_t *accepts, uint64_t *sweeps) {
@@ -1037,10 +1154,11 @@ extern "C" su3_status su3_action(su3_lattice *lat, double *booked, double *direc
   LAT_CHECK(lat);
   Engine &e = lat->eng;
   if (e.tiles_dirty) TRY(e.rebuild());
-  double dS = 0.0, S = 0.0;
+  double dS = 0.0, S = 0.0, ref = 0.0;
   TRY(e.booked_change(0, &dS));
+  TRY(e.action_reference(0, &ref));
   TRY(e.direct_action(0, &S));
-  if (booked) *booked = e.chains[0].action_ref + dS;
+  if (booked) *booked = ref + dS;
   if (direct) *direct = S;
   return SU3_OK;
 }

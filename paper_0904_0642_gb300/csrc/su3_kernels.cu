@@ -809,6 +809,38 @@ __global__ void k_sub_copy(const ChainDesc *sub_dev, const ChainDesc *plain_dev,
   }
 }
 
+// Links given as rows 1 and 2 in float (12 per link, canonical site order:
+// [layer][i_s - 1][mu][row][col][re, im]); row 3 = conj(row1 x row2).
+template <class S>
+__global__ void k_convert_rows2(ChainDesc *desc_dev, const float *src) {
+  const ChainDesc d = *desc_dev;
+  const size_t nlinks = (size_t)d.nlayers * d.V * d.D;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nlinks; i += (size_t)gridDim.x * blockDim.x) {
+    const int mu = (int)(i % d.D);
+    const size_t ls = i / d.D;
+    const int s = (int)(ls % d.V);
+    const int layer = (int)(ls / d.V);
+    int r = s, sum = 0;
+    for (int k = 0; k < d.D; ++k) {
+      const int n = d.dims[k];
+      sum += r % n;
+      r /= n;
+    }
+    const float4 *c = reinterpret_cast<const float4 *>(src + i * 12);
+    const float4 q0 = c[0], q1 = c[1], q2 = c[2];
+    using R = typename S::R;
+    M3<R> m;
+    m.e[0][0] = {(R)q0.x, (R)q0.y};
+    m.e[0][1] = {(R)q0.z, (R)q0.w};
+    m.e[0][2] = {(R)q1.x, (R)q1.y};
+    m.e[1][0] = {(R)q1.z, (R)q1.w};
+    m.e[1][1] = {(R)q2.x, (R)q2.y};
+    m.e[1][2] = {(R)q2.z, (R)q2.w};
+    third_row(m);
+    S::store(plane_ptr<S>(d, layer, sum & 1, mu), d.Vh, s >> 1, m);
+  }
+}
+
 // ------------------------------------------------------------------ measurement without allocation
 // For callers that cannot allocate device memory (see su3_measure_noalloc):
 // the per-tile partial sums go to a fixed array in the library's own device
@@ -973,6 +1005,16 @@ cudaError_t launch_start(int storage, ChainDesc *desc_dev, size_t nlinks, int ho
     k_start<StoreF64x18><<<grid, block, 0, st>>>(desc_dev, hot);
   else
     k_start<StoreF32x12><<<grid, block, 0, st>>>(desc_dev, hot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_rows2(int storage, ChainDesc *desc_dev, size_t nlinks, const float *src, cudaStream_t st) {
+  const int block = 256;
+  const int grid = (int)((nlinks + block - 1) / block < 65536 ? (nlinks + block - 1) / block : 65536);
+  if (storage == 0)
+    k_convert_rows2<StoreF64x18><<<grid, block, 0, st>>>(desc_dev, src);
+  else
+    k_convert_rows2<StoreF32x12><<<grid, block, 0, st>>>(desc_dev, src);
   return cudaGetLastError();
 }
 

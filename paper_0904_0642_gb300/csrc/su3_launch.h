@@ -27,6 +27,8 @@ cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, in
 cudaError_t launch_start(int storage, ChainDesc *desc_dev, size_t nlinks, int hot, cudaStream_t st);
 cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, double *canon, int to_canonical,
                            cudaStream_t st);
+// Links from rows 1, 2 in float (12 per link, canonical order; 16-byte aligned).
+cudaError_t launch_convert_rows2(int storage, ChainDesc *desc_dev, size_t nlinks, const float *src, cudaStream_t st);
 cudaError_t tick_occupancy(int storage, int variant, bool weighted, bool sub, int block, int *ctas_per_sm);
 void host_advance_stage(const ChainDesc &d, ChainState &s);
 // Fixed-order sum of n booked action-change slots into *out (device).
