@@ -223,39 +223,58 @@ __device__ __forceinline__ double rsqrt_d(double n) {
   return y;
 }
 
-// Gram-Schmidt of rows 1, 2 in double, row 3 from the cross product.
-template <int NEWTON = 2>
+// Gram-Schmidt of rows 1, 2 in double, row 3 from the cross product
+// (ROW3 = false: rows 1, 2 only, for storage that keeps two rows).  Written
+// as explicit FMA chains: FP64 is the scarce pipe on this GPU, and
+// `s += a*b + c*d` would cost a multiply, an FMA and an add.
+template <int NEWTON = 2, bool ROW3 = true>
 __device__ __forceinline__ void reunit_d(M3<double> &m) {
-  double n1 = 0;
+  C<double> *r1 = m.e[0], *r2 = m.e[1];
+  double n1 = r1[0].re * r1[0].re;
+  n1 = fm(r1[0].im, r1[0].im, n1);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) n1 += m.e[0][k].re * m.e[0][k].re + m.e[0][k].im * m.e[0][k].im;
-  double i1 = rsqrt_d<NEWTON>(n1);
+  for (int k = 1; k < 3; ++k) {
+    n1 = fm(r1[k].re, r1[k].re, n1);
+    n1 = fm(r1[k].im, r1[k].im, n1);
+  }
+  const double i1 = rsqrt_d<NEWTON>(n1);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    m.e[0][k].re *= i1;
-    m.e[0][k].im *= i1;
+    r1[k].re *= i1;
+    r1[k].im *= i1;
   }
-  double pr = 0, pi = 0;  // <r1, r2> = sum conj(r1_k) r2_k
+  // <r1, r2> = sum_k conj(r1_k) r2_k
+  double pr = r1[0].re * r2[0].re, pi = r1[0].re * r2[0].im;
+  pr = fm(r1[0].im, r2[0].im, pr);
+  pi = fm(-r1[0].im, r2[0].re, pi);
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    pr = fm(r1[k].re, r2[k].re, pr);
+    pr = fm(r1[k].im, r2[k].im, pr);
+    pi = fm(r1[k].re, r2[k].im, pi);
+    pi = fm(-r1[k].im, r2[k].re, pi);
+  }
+  // r2 -= <r1, r2> r1
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    pr += m.e[0][k].re * m.e[1][k].re + m.e[0][k].im * m.e[1][k].im;
-    pi += m.e[0][k].re * m.e[1][k].im - m.e[0][k].im * m.e[1][k].re;
+    const double re = r1[k].re, im = r1[k].im;
+    r2[k].re = fm(-pr, re, fm(pi, im, r2[k].re));
+    r2[k].im = fm(-pr, im, fm(-pi, re, r2[k].im));
   }
+  double n2 = r2[0].re * r2[0].re;
+  n2 = fm(r2[0].im, r2[0].im, n2);
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    n2 = fm(r2[k].re, r2[k].re, n2);
+    n2 = fm(r2[k].im, r2[k].im, n2);
+  }
+  const double i2 = rsqrt_d<NEWTON>(n2);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    m.e[1][k].re -= pr * m.e[0][k].re - pi * m.e[0][k].im;
-    m.e[1][k].im -= pr * m.e[0][k].im + pi * m.e[0][k].re;
+    r2[k].re *= i2;
+    r2[k].im *= i2;
   }
-  double n2 = 0;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) n2 += m.e[1][k].re * m.e[1][k].re + m.e[1][k].im * m.e[1][k].im;
-  double i2 = rsqrt_d<NEWTON>(n2);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    m.e[1][k].re *= i2;
-    m.e[1][k].im *= i2;
-  }
-  third_row(m);
+  if constexpr (ROW3) third_row(m);
 }
 
 template <typename A, typename B>

@@ -250,15 +250,43 @@ __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, 
 
 // ------------------------------------------------------------------ re-unitarisation
 
+// Rows 1, 2 of a stored link in double (row 3 is rebuilt by reunit_d, or
+// not kept at all by two-row storage).
+template <class S>
+__device__ __forceinline__ M3<double> load_rows2_d(const typename S::Vec *p, int Vh, int js) {
+  const M3<typename S::R> f = S::load2(p, Vh, js);
+  M3<double> m;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      m.e[i][j] = i < 2 ? C<double>{(double)f.e[i][j].re, (double)f.e[i][j].im} : C<double>{0.0, 0.0};
+  return m;
+}
+
+// Two links per step: their Gram-Schmidt chains are independent.
 template <class S, bool SUB = false>
 __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int jj) {
+  constexpr bool kTwoRows = sizeof(typename S::R) == 4;  // FP32 storage keeps rows 1, 2 only
+  constexpr int kNewton = kTwoRows ? 1 : 2;
   const int Vh = d.Vh;
   for (int colour = 0; colour < 2; ++colour) {
     const int js = SUB ? (site_of<true>(d, layer, colour, jj).s >> 1) : jj;
-    for (int mu = 0; mu < d.D; ++mu) {
+    int mu = 0;
+#pragma unroll 1
+    for (; mu + 1 < d.D; mu += 2) {
+      typename S::Vec *p0 = plane_ptr<S>(d, layer, colour, mu), *p1 = plane_ptr<S>(d, layer, colour, mu + 1);
+      M3<double> m0 = load_rows2_d<S>(p0, Vh, js);
+      M3<double> m1 = load_rows2_d<S>(p1, Vh, js);
+      reunit_d<kNewton, !kTwoRows>(m0);
+      reunit_d<kNewton, !kTwoRows>(m1);
+      S::store(p0, Vh, js, m3_cast<typename S::R>(m0));
+      S::store(p1, Vh, js, m3_cast<typename S::R>(m1));
+    }
+    if (mu < d.D) {
       typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
-      M3<double> m = m3_cast<double>(S::load(p, Vh, js));
-      reunit_d<sizeof(typename S::R) == 4 ? 1 : 2>(m);
+      M3<double> m = load_rows2_d<S>(p, Vh, js);
+      reunit_d<kNewton, !kTwoRows>(m);
       S::store(p, Vh, js, m3_cast<typename S::R>(m));
     }
   }
