@@ -470,7 +470,11 @@ __device__ __forceinline__ void flush_counters(const ChainDesc &d, uint32_t &np,
 // the 2D update phases of a sweep, then a re-unitarisation and/or a
 // measurement when the completed-sweep count is a multiple of their
 // cadence; the chain goes idle when a sweep would start at its target.
-__device__ __host__ inline void advance_stage(const ChainDesc &d, ChainState &s) {
+struct StageParams {
+  int D, reunit_every, measure_every;
+};
+
+__device__ __host__ inline void advance_stage(const StageParams &d, ChainState &s) {
   s.prev_stage = s.stage;
   if (s.stage < 2 * d.D) {
     s.stage += 1;
@@ -487,6 +491,10 @@ __device__ __host__ inline void advance_stage(const ChainDesc &d, ChainState &s)
     s.stage = 0;
   }
   if (s.stage == 0 && s.sweep >= s.target) s.active = 0;
+}
+
+__device__ __host__ inline void advance_stage(const ChainDesc &d, ChainState &s) {
+  advance_stage(StageParams{d.D, d.reunit_every, d.measure_every}, s);
 }
 
 // Register variants of the tick kernel: __launch_bounds__(threads, CTAs per
@@ -574,25 +582,56 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
   if (prev != gridDim.x * (blockDim.x >> 5) - 1) return;
   __threadfence();
   const int nchains = ea.hdr->nchains;
-  for (int c = 0; c < nchains; ++c) {
-    const ChainState st = ea.state[c];
-    if (st.active && st.stage == kStageMeasure) {
-      const ChainDesc &d = ea.desc[c];
-      double *out = d.results + (size_t)(st.n_meas % (uint32_t)d.result_cap) * (d.nlayers + 1) * kMeasVals;
+  // chains in a measurement stage: 32 states read at a time (one lane each),
+  // then each such chain finished by the whole warp
+  for (int base = 0; base < nchains; base += 32) {
+    const int c = base + lane;
+    bool meas = false;
+    uint32_t nm = 0;
+    if (c < nchains) {
+      const ChainState st = ea.state[c];
+      meas = st.active && st.stage == kStageMeasure;
+      nm = st.n_meas;
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, meas);
+    while (todo) {
+      const int k = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t n_meas = __shfl_sync(0xffffffffu, nm, k);
+      const ChainDesc &d = ea.desc[base + k];
+      double *out = d.results + (size_t)(n_meas % (uint32_t)d.result_cap) * (d.nlayers + 1) * kMeasVals;
       finalize_measure(d, d.partials, out);
     }
   }
   __syncwarp();
   __threadfence();
-  for (int c = lane; c < nchains; c += 32) {
-    ChainState st = ea.state[c];
-    if (!st.active) {
-      if (st.prev_stage != -1) ea.state[c].prev_stage = -1;  // nothing ran: no halo refresh
-      continue;
+  // advance every chain's stage machine: four chains per lane in flight, so
+  // that their loads overlap
+  constexpr int kU = 4;
+  for (int base = lane; base < nchains; base += 32 * kU) {
+    ChainState st[kU];
+    StageParams sp[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int c = base + 32 * u;
+      if (c < nchains) {
+        st[u] = ea.state[c];
+        const ChainDesc &d = ea.desc[c];
+        sp[u] = StageParams{d.D, d.reunit_every, d.measure_every};
+      }
     }
-    if (st.stage == kStageMeasure) st.n_meas += 1;
-    advance_stage(ea.desc[c], st);
-    ea.state[c] = st;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int c = base + 32 * u;
+      if (c >= nchains) continue;
+      if (!st[u].active) {
+        if (st[u].prev_stage != -1) ea.state[c].prev_stage = -1;  // nothing ran: no halo refresh
+        continue;
+      }
+      if (st[u].stage == kStageMeasure) st[u].n_meas += 1;
+      advance_stage(sp[u], st[u]);
+      ea.state[c] = st[u];
+    }
   }
   if (lane == 0) ea.hdr->done_warps = 0;
 }
