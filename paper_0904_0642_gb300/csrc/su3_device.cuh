@@ -409,6 +409,33 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 __device__ __forceinline__ float unif_f(uint32_t w) { return __fmaf_rn(__uint2float_rn(w), 0x1p-32f, 0x1p-33f); }
 __device__ __forceinline__ double unif_d(uint32_t w) { return __fma_rn((double)w, 0x1p-32, 0x1p-33); }
 
+// Approximate (SFU) square root and reciprocal for the FP32 draw: their
+// relative errors (a few 1e-7) stay inside the FP32 rounding of the link.
+// sqrt.approx of 0 is 0.
+__device__ __forceinline__ float sqrt_sfu(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_sfu(float x) {
+  float y;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// |a| and 1/|a| of the projection: IEEE sqrt and division in double; in
+// float one SFU reciprocal square root gives both.
+__device__ __forceinline__ void norm_and_inverse(double n, double &k, double &ik) {
+  k = sqrt(n);
+  ik = 1.0 / k;
+}
+__device__ __forceinline__ void norm_and_inverse(float n, float &k, float &ik) {
+  float r;
+  asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(n));
+  ik = r;
+  k = n * r;
+}
+
 __device__ __forceinline__ uint32_t heatbath_tag(int colour, int mu, int subgroup) {
   return ((uint32_t)subgroup << 8) | ((uint32_t)mu << 10) | ((uint32_t)colour << 14);
 }
@@ -468,7 +495,7 @@ __device__ __forceinline__ bool su2_draw(float alpha, int hits, uint2 key, uint3
   // as 2 pi (u - 1/2) - the sign flip is absorbed - to stay on [-pi, pi].
   float X = 0.0f;
   bool acc = false;
-  const float ia = 1.0f / alpha;
+  const float ia = rcp_sfu(alpha);
   for (int h = 0; h < hits; ++h) {
     const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | (uint32_t)h, kPurposeHeatbath), key);
     ++nprop;
@@ -483,12 +510,12 @@ __device__ __forceinline__ bool su2_draw(float alpha, int hits, uint2 key, uint3
   if (!acc) return false;
   const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | kHitDirection, kPurposeHeatbath), key);
   const float costh = 2.0f * unif_f(w.x) - 1.0f;
-  const float sinth = sqrtf(1.0f - costh * costh);
+  const float sinth = sqrt_sfu(1.0f - costh * costh);
   float sphi, cphi;
   __sincosf(__fmaf_rn(unif_f(w.y), 6.28318530717958648f, -3.14159265358979324f), &sphi, &cphi);
   sphi = -sphi;  // sin(2 pi u) = -sin(2 pi (u - 1/2)), likewise cos
   cphi = -cphi;
-  const float rho = sqrtf(X * (2.0f - X));
+  const float rho = sqrt_sfu(X * (2.0f - X));
   x[0] = 1.0f - X;
   x[1] = rho * sinth * cphi;
   x[2] = rho * sinth * sphi;
@@ -561,20 +588,21 @@ __device__ __forceinline__ void cm_update(M3<R> &U, const M3<R> &A, R beta, int 
                                           uint32_t c1, int colour, int mu, uint32_t &nprop, uint32_t &nacc,
                                           R &dretr) {
   dretr = R(0);
+  const R ca = R(2) * beta / R(3);  // alpha = (2 beta / 3) k
 #pragma unroll
   for (int sg = 0; sg < 3; ++sg) {
     const int i = (sg == 2) ? 1 : 0;
     const int j = (sg == 0) ? 1 : 2;
     R a0, a1, a2, a3;
     block_projection(U, A, i, j, a0, a1, a2, a3);
-    const R k = sqrt(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3);
+    R k, ik;
+    norm_and_inverse(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3, k, ik);
     if (!(k > (sizeof(R) == 4 ? R(1e-30) : R(1e-300)))) continue;
-    const R alpha = R(2) * beta * k / R(3);
+    const R alpha = ca * k;
     R x[4];
     if (!su2_draw(alpha, hits, key, c0, c1, heatbath_tag(colour, mu, sg), x, nprop)) continue;
     ++nacc;
     dretr += R(2) * (k * x[0] - a0);
-    const R ik = R(1) / k;
     const R v0 = a0 * ik, v1 = a1 * ik, v2 = a2 * ik, v3 = a3 * ik;
     // r = x v^+ as quaternions: r0 = x0 v0 + x.v, r = -x0 v + v0 x + x cross v
     const R r0 = x[0] * v0 + x[1] * v1 + x[2] * v2 + x[3] * v3;
