@@ -191,13 +191,54 @@ struct Chain {
   void *plain = nullptr;
   ChainDesc pdesc{};
   ChainDesc *d_pdesc = nullptr;
+  int4 *d_halo = nullptr;  // halo sites of a box (see ChainDesc::halo)
+  int halo_n[2] = {0, 0};
 };
+
+// Halo sites of one sublattice box, colour 0 then colour 1 (every box has
+// the same local geometry): padded index, the owner's padded index, and the
+// owner's box as an offset of -1 / 0 / +1 per direction (2 bits each).
+// d describes the padded box.  A low halo site (padded coordinate 0) is the
+// last interior site of the previous box, a high one the first interior
+// site of the next box.
+static std::vector<int4> halo_list(const ChainDesc &d, int n[2]) {
+  std::vector<int4> col[2];
+  const int Vpad = 2 * d.Vh;
+  for (int sp = 0; sp < Vpad; ++sp) {
+    int r = sp, halo = 0, par = 0, src = 0, code = 0;
+    for (int k = 0; k < d.D; ++k) {
+      const int x = r % d.dims[k];
+      r /= d.dims[k];
+      int xs = x, c = 0;
+      if (d.hpad[k] && x == 0) {
+        halo = 1;
+        xs = d.idims[k];
+        c = 1;
+      } else if (d.hpad[k] && x == d.dims[k] - 1) {
+        halo = 1;
+        xs = 1;
+        c = 2;
+      }
+      par += x - d.hpad[k] + 2;  // colour: parity of the coordinates in the undivided lattice
+      src += xs * d.stride[k];
+      code |= c << (2 * k);
+    }
+    if (halo) col[par & 1].push_back(make_int4(sp, src, code, 0));
+  }
+  n[0] = (int)col[0].size();
+  n[1] = (int)col[1].size();
+  col[0].insert(col[0].end(), col[1].begin(), col[1].end());
+  return col[0];
+}
 
 static void fill_desc(Chain &ch, int tile) {
   const su3_config &c = ch.cfg;
   ChainDesc &d = ch.desc;
   d.links = ch.links;
   d.action_slots = ch.action_slots;
+  d.halo = ch.d_halo;
+  d.halo_n[0] = ch.halo_n[0];
+  d.halo_n[1] = ch.halo_n[1];
   d.results = ch.results;
   d.partials = ch.partials;
   d.counters = ch.counters;
@@ -411,8 +452,10 @@ struct Engine {
     if (ch.own_links) cudaFree(ch.links);
     cudaFree(ch.plain);
     cudaFree(ch.d_pdesc);
+    cudaFree(ch.d_halo);
     ch.plain = nullptr;
     ch.d_pdesc = nullptr;
+    ch.d_halo = nullptr;
     cudaFree(ch.results);
     cudaFree(ch.partials);
     cudaFree(ch.counters);
@@ -457,6 +500,13 @@ struct Engine {
         return fail(SU3_ENOMEM, "descriptor allocation failed");
       }
       ch.bytes_total += pb + sizeof(ChainDesc);
+      const std::vector<int4> hl = halo_list(ch.desc, ch.halo_n);
+      if (cudaMalloc(&ch.d_halo, hl.size() * sizeof(int4)) != cudaSuccess) {
+        free_chain(ch);
+        return fail(SU3_ENOMEM, "halo list allocation failed");
+      }
+      CU(cudaMemcpy(ch.d_halo, hl.data(), hl.size() * sizeof(int4), cudaMemcpyHostToDevice));
+      ch.bytes_total += hl.size() * sizeof(int4);
     }
     if (cfg.link_buffer) {
       if (cfg.link_buffer_bytes < ch.link_bytes)
@@ -526,7 +576,7 @@ struct Engine {
       ChainState *ds = nullptr;
       CU(cudaMallocAsync(&ds, sizeof(ChainState), stream));
       CU(cudaMemsetAsync(ds, 0, sizeof(ChainState), stream));
-      CU(launch_halo(storage, dd, ds, 1, (long long)ch.desc.nlayers * ch.desc.nb * 2 * ch.desc.Vh, stream));
+      CU(launch_halo(storage, dd, ds, 1, ch.desc.nlayers * ch.desc.nb, ch.halo_n[0] + ch.halo_n[1], stream));
       CU(cudaFreeAsync(ds, stream));
     } else {
       CU(launch_start(storage, dd, nlinks, ch.cfg.start == SU3_START_HOT, stream));
@@ -646,16 +696,16 @@ struct Engine {
 
   EngineArgs args() const { return EngineArgs{d_desc, d_state, d_hdr, d_tile_chain}; }
 
-  // Sites of all sublattice boxes of a divided chain (the only chain of its engine).
-  long long padded_sites() const {
-    const ChainDesc &d = chains[0].desc;
-    return (long long)d.nlayers * d.nb * 2 * d.Vh;
+  // Halo refresh of the (only) chain of an engine with a divided chain.
+  cudaError_t halo_refresh(ChainDesc *dd, ChainState *ds, int all) const {
+    const Chain &ch = chains[0];
+    return launch_halo(storage, dd, ds, all, ch.desc.nlayers * ch.desc.nb, ch.halo_n[0] + ch.halo_n[1], stream);
   }
 
   // One tick, and for a divided chain the halo refresh of what it changed.
   su3_status one_tick(int grid) {
     CU(launch_tick(storage, variant, weighted_any, sub_any, args(), grid, block, stream));
-    if (sub_any) CU(launch_halo(storage, d_desc, d_state, 0, padded_sites(), stream));
+    if (sub_any) CU(halo_refresh(d_desc, d_state, 0));
     return SU3_OK;
   }
 
@@ -665,7 +715,7 @@ struct Engine {
     Chain &ch = chains[c];
     const size_t nlinks = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
     CU(launch_sub_copy(storage, d_desc + c, ch.d_pdesc, nlinks, to_sub, stream));
-    if (to_sub) CU(launch_halo(storage, d_desc + c, d_state + c, 1, padded_sites(), stream));
+    if (to_sub) CU(halo_refresh(d_desc + c, d_state + c, 1));
     return SU3_OK;
   }
 
@@ -699,7 +749,7 @@ struct Engine {
     CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kGraphTicks; ++i) {
       cudaError_t e = launch_tick(storage, variant, weighted_any, sub_any, args(), grid, block, stream);
-      if (e == cudaSuccess && sub_any) e = launch_halo(storage, d_desc, d_state, 0, padded_sites(), stream);
+      if (e == cudaSuccess && sub_any) e = halo_refresh(d_desc, d_state, 0);
       if (e != cudaSuccess) {
         cudaStreamEndCapture(stream, &g);
         if (g) cudaGraphDestroy(g);

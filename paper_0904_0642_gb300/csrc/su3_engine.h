@@ -9,6 +9,7 @@
 // share a launch.
 #pragma once
 #include <cstdint>
+#include <cuda_runtime.h>
 
 namespace su3g {
 
@@ -70,6 +71,11 @@ struct ChainDesc {
   int32_t hpad[kMaxD];       // 1: divided direction, one halo layer on each side
   int32_t bdiv[kMaxD];       // sublattices per direction
   int32_t gstride[kMaxD];    // strides of the undivided layer
+  // Halo sites of a box (the same for every box), colour 0 first then
+  // colour 1: {padded index, owner's padded index, owner box offset code
+  // (2 bits per direction: 0 same box, 1 previous, 2 next), 0}.
+  const int4 *halo;
+  int32_t halo_n[2];
   float beta_f;
   double beta_d;
   // DLT with two couplings (Sec. 2.2): weighted = 1 when beta1 != beta; a

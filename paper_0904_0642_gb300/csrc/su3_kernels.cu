@@ -764,53 +764,13 @@ __global__ void k_convert(ChainDesc *desc_dev, double *canon, int to_canonical) 
 // double-layered torus lands in the other layer).  Halo sites are never
 // sources, so the copies do not race.
 
-// Undivided coordinates of a padded-box site; returns false for interior
-// sites.  Sets the owner's virtual layer, padded index and the colour.
-__device__ __forceinline__ bool halo_owner(const ChainDesc &d, int vl, int sp, int &vsrc, int &spsrc, int &colour) {
-  int r = sp, xp[kMaxD];
-  bool halo = false;
-#pragma unroll
-  for (int k = 0; k < kMaxD; ++k) {
-    xp[k] = 0;
-    if (k < d.D) {
-      xp[k] = r % d.dims[k];
-      r /= d.dims[k];
-      if (d.hpad[k] && (xp[k] == 0 || xp[k] == d.dims[k] - 1)) halo = true;
-    }
-  }
-  if (!halo) return false;
-  const int L = vl / d.nb;
-  int b = vl - L * d.nb, flip = 0, bsrc = 0, bmul = 1, par = 0;
-  spsrc = 0;
-#pragma unroll
-  for (int k = 0; k < kMaxD; ++k)
-    if (k < d.D) {
-      const int bc = b % d.bdiv[k];
-      b /= d.bdiv[k];
-      const int n = d.idims[k] * d.bdiv[k];
-      const int glued = d.nlayers == 2 ? ((d.glue_mask >> k) & 1) : 0;
-      int gx = bc * d.idims[k] + xp[k] - d.hpad[k];
-      if (gx < 0) {
-        gx += n;
-        flip ^= glued;
-      } else if (gx >= n) {
-        gx -= n;
-        flip ^= glued;
-      }
-      par += gx;
-      const int bo = gx / d.idims[k];
-      bsrc += bo * bmul;
-      bmul *= d.bdiv[k];
-      spsrc += (gx - bo * d.idims[k] + d.hpad[k]) * d.stride[k];
-    }
-  vsrc = (L ^ flip) * d.nb + bsrc;
-  colour = par & 1;
-  return true;
-}
-
 // Refresh the halos of a divided chain: all links (all = 1, after a start,
 // set_links or re-unitarisation) or, after an update tick, only the
-// (colour, direction) that the tick changed.
+// (colour, direction) that the tick changed.  Threads run over the box's
+// list of halo sites of that colour (blockIdx.y = box): the owner is the
+// same padded site of the neighbouring box given by the entry's offset
+// code, whose box coordinate wraps periodically; a wrap across a glued
+// boundary of the double-layered torus lands in the other layer.
 template <class S>
 __global__ void k_halo(const ChainDesc *desc_dev, const ChainState *state_dev, int all) {
   const ChainDesc &d = *desc_dev;
@@ -826,15 +786,39 @@ __global__ void k_halo(const ChainDesc *desc_dev, const ChainState *state_dev, i
       return;  // a measurement, or nothing ran: no link changed
     }
   }
-  const int Vpad = 2 * d.Vh;
-  const long long n = (long long)d.nlayers * d.nb * Vpad;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int vl = (int)(i / Vpad), sp = (int)(i - (long long)vl * Vpad);
-    int vsrc, spsrc, colour;
-    if (!halo_owner(d, vl, sp, vsrc, spsrc, colour) || colour < c0 || colour >= c1) continue;
+  const int vl = blockIdx.y;
+  const int L = vl / d.nb;
+  int bc[kMaxD], rest = vl - L * d.nb;
+#pragma unroll
+  for (int k = 0; k < kMaxD; ++k) {
+    bc[k] = 0;
+    if (k < d.D) {
+      bc[k] = rest % d.bdiv[k];
+      rest /= d.bdiv[k];
+    }
+  }
+  const int first = c0 == 0 ? 0 : d.halo_n[0];
+  const int count = (c0 == 0 ? d.halo_n[0] : 0) + (c1 == 2 ? d.halo_n[1] : 0);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    const int4 h = d.halo[first + e];
+    const int colour = (first + e) < d.halo_n[0] ? 0 : 1;
+    int bsrc = 0, bmul = 1, flip = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxD; ++k)
+      if (k < d.D) {
+        const int code = (h.z >> (2 * k)) & 3;
+        int o = bc[k] + (code == 1 ? -1 : (code == 2 ? 1 : 0));
+        if (o < 0 || o >= d.bdiv[k]) {
+          o = o < 0 ? o + d.bdiv[k] : o - d.bdiv[k];
+          if (d.nlayers == 2) flip ^= (d.glue_mask >> k) & 1;
+        }
+        bsrc += o * bmul;
+        bmul *= d.bdiv[k];
+      }
+    const int vsrc = (L ^ flip) * d.nb + bsrc;
     for (int mu = m0; mu < m1; ++mu) {
-      typename S::Vec *dst = plane_ptr<S>(d, vl, colour, mu) + (sp >> 1);
-      const typename S::Vec *src = plane_ptr<S>(d, vsrc, colour, mu) + (spsrc >> 1);
+      typename S::Vec *dst = plane_ptr<S>(d, vl, colour, mu) + (h.x >> 1);
+      const typename S::Vec *src = plane_ptr<S>(d, vsrc, colour, mu) + (h.y >> 1);
 #pragma unroll
       for (int q = 0; q < S::NQ; ++q) dst[(size_t)q * d.Vh] = src[(size_t)q * d.Vh];
     }
@@ -1032,11 +1016,11 @@ cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, const
                   : launch_tick_w<false>(storage, variant, sub, ea, grid, block, st);
 }
 
-cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, int all,
-                        long long padded_sites, cudaStream_t st) {
+cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, int all, int boxes,
+                        int halo_sites, cudaStream_t st) {
   const int block = 256;
-  const long long want = (padded_sites + block - 1) / block;
-  const int grid = (int)(want < 16384 ? (want > 0 ? want : 1) : 16384);
+  const dim3 grid((unsigned)((halo_sites + block - 1) / block > 0 ? (halo_sites + block - 1) / block : 1),
+                  (unsigned)boxes);
   if (storage == 0)
     k_halo<StoreF64x18><<<grid, block, 0, st>>>(desc_dev, state_dev, all);
   else
