@@ -246,6 +246,30 @@ def bench_ensemble(su3, torch, stream):
             "plaquette_mean": float(meas[:, 0].mean())}
 
 
+def bench_divided(su3, torch, stream):
+    """The 32^4 workload on a lattice cut into 2^4 sublattice boxes with
+    halo exchange (the paper's MPI decomposition, on one device), against
+    the undivided lattice: 10 sweeps + re-unitarisation per step."""
+    out = {}
+    for name, ndiv in (("undivided", [1, 1, 1, 1]), ("2x2x2x2", [2, 2, 2, 2])):
+        lat = su3.Lattice(DIMS, beta=BETA, seed=SEED, hits=HITS, storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT,
+                          reunit_every=SWEEPS_PER_STEP, ndiv=ndiv, stream=stream)
+        lat.autotune()
+        lat.sweep(SWEEPS_PER_STEP)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            lat.sweep(SWEEPS_PER_STEP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = 3 * SWEEPS_PER_STEP * lat.nlinks / (e0.elapsed_time(e1) * 1e-3)
+        lat.close()
+    return {"workload": "32^4 PBC beta=6 FP32, cut into 2x2x2x2 sublattice boxes (16^4 interiors + halos)",
+            "value": out["2x2x2x2"], "unit": UNIT, "undivided": out["undivided"],
+            "ratio": out["2x2x2x2"] / out["undivided"]}
+
+
 def bench_dlt_and_d3(su3, torch, stream):
     out = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -501,6 +525,7 @@ def main():
         lat64.close()
         if rank == 0 and world == 1:
             line["ensemble_256x8^4"] = bench_ensemble(su3, torch, stream)
+            line["divided_32^4_2x2x2x2"] = bench_divided(su3, torch, stream)
             line.update(bench_dlt_and_d3(su3, torch, stream))
             line["serving"] = bench_serving(su3, torch)
 
