@@ -508,8 +508,9 @@ def main():
                             start=su3.SU3_START_HOT, reunit_every=SWEEPS_PER_STEP, stream=stream)
         lat64.sweep(SWEEPS_PER_STEP)
         ref32.sweep(SWEEPS_PER_STEP)
-        p64 = lat64.plaquette()[0]
-        p32 = ref32.plaquette()[0]
+        p64, s64, t64 = lat64.plaquette()
+        p32, s32, t32 = ref32.plaquette()
+        l64, l32 = lat64.polyakov(), ref32.polyakov()
         torch.cuda.synchronize()
         k64 = 3
         e0.record(stream)
@@ -521,6 +522,9 @@ def main():
         line["fp64_single_chain"] = {"value": world * k64 * SWEEPS_PER_STEP * links / (ms64 * 1e-3), "unit": UNIT,
                                      "steps": k64, "storage": "FP64 18-real"}
         line["plaquette_fp32_vs_fp64_after_10_sweeps"] = {"fp32": p32, "fp64": p64, "abs_diff": abs(p32 - p64)}
+        line["fp32_vs_fp64_after_10_sweeps"] = {  # same start and random numbers; every observable
+            "plaquette": abs(p32 - p64), "space": abs(s32 - s64), "time": abs(t32 - t64),
+            "polyakov": abs(l32 - l64), "polyakov_fp64": [l64.real, l64.imag]}
         ref32.close()
         lat64.close()
         if rank == 0 and world == 1:
