@@ -131,33 +131,6 @@ __device__ __forceinline__ M3<R> mul_nd_2(const M3<R> &a, const M3<R> &b) { retu
 template <typename R>
 __device__ __forceinline__ M3<R> mul_dn_2(const M3<R> &a, const M3<R> &b) { return mul_dn<2>(a, b); }
 
-template <typename R>
-__device__ __forceinline__ void m3_acc(M3<R> &a, const M3<R> &b) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      a.e[i][j].re += b.e[i][j].re;
-      a.e[i][j].im += b.e[i][j].im;
-    }
-}
-
-// Re Tr(a b^+) = sum_ij Re(a_ij conj(b_ij))
-template <typename R>
-__device__ __forceinline__ R retr_nd(const M3<R> &a, const M3<R> &b) {
-  R s = a.e[0][0].re * b.e[0][0].re;
-  s = fm(a.e[0][0].im, b.e[0][0].im, s);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      if (i == 0 && j == 0) continue;
-      s = fm(a.e[i][j].re, b.e[i][j].re, s);
-      s = fm(a.e[i][j].im, b.e[i][j].im, s);
-    }
-  return s;
-}
-
 // conj(p q - r s)
 template <typename R>
 __device__ __forceinline__ C<R> conj_cross(const C<R> &p, const C<R> &q, const C<R> &r, const C<R> &s) {
