@@ -453,27 +453,36 @@ __device__ __forceinline__ bool su2_draw(double alpha, int hits, uint2 key, uint
   return su2_draw_d(alpha, hits, key, c0, c1, tag, x, nprop);
 }
 
-__device__ __forceinline__ bool su2_draw(float alpha, int hits, uint2 key, uint32_t c0, uint32_t c1, uint32_t tag,
-                                         float x[4], uint32_t &nprop) {
-  if (alpha >= kAlphaFp64) {
-    double xd[4];
-    const bool a = su2_draw_d((double)alpha, hits, key, c0, c1, tag, xd, nprop);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) x[i] = (float)xd[i];
-    return a;
-  }
-  // The float draw uses the SFU forms of ln, sin and cos: their absolute
-  // errors (~2e-7 for ln, ~4e-7 for sin/cos on [-pi, pi]) stay well inside
-  // the FP32 storage rounding of the updated link.  Angles 2 pi u are taken
-  // as 2 pi (u - 1/2) - the sign flip is absorbed - to stay on [-pi, pi].
+// ln u of the uniform (w + 1/2) / 2^32, accurate relative to ln u for
+// every word: for u above 1/2 from the exact small complement,
+// ln u = log1p(-(2^32 - 1 - w + 1/2) / 2^32), so that u near 1 keeps its
+// digits (the float u itself is quantised there to ~6e-8).
+__device__ __forceinline__ float log_unif_accurate(uint32_t w) {
+  if (w & 0x80000000u) return log1pf(-__fmaf_rn(__uint2float_rn(0xFFFFFFFFu - w), 0x1p-32f, 0x1p-33f));
+  return logf(unif_f(w));
+}
+
+// The float draw.  ACCURATE = false: the SFU forms of ln and cos, whose
+// absolute errors (~3.6e-7 for ln on [0.5, 1], ~4e-7 for cos on [-pi, pi])
+// enter X = -(ln u1 + cos^2 ln u3) / alpha divided by alpha: inside the FP32
+// storage rounding for alpha >= 2.  ACCURATE = true (small alpha, strong
+// coupling): cosf and a logarithm accurate relative to ln u even for u near
+// 1 (log_unif_accurate), which keep X to ~1e-7 relative for any alpha.  Angles 2 pi u are taken as 2 pi (u - 1/2) - the sign flip
+// is absorbed - to stay on [-pi, pi].
+template <bool ACCURATE>
+__device__ __forceinline__ bool su2_draw_f(float alpha, int hits, uint2 key, uint32_t c0, uint32_t c1, uint32_t tag,
+                                           float x[4], uint32_t &nprop) {
   float X = 0.0f;
   bool acc = false;
   const float ia = rcp_sfu(alpha);
   for (int h = 0; h < hits; ++h) {
     const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | (uint32_t)h, kPurposeHeatbath), key);
     ++nprop;
-    const float cs = __cosf(__fmaf_rn(unif_f(w.y), 6.28318530717958648f, -3.14159265358979324f));
-    X = -(__logf(unif_f(w.x)) + cs * cs * __logf(unif_f(w.z))) * ia;
+    const float ang = __fmaf_rn(unif_f(w.y), 6.28318530717958648f, -3.14159265358979324f);
+    const float cs = ACCURATE ? cosf(ang) : __cosf(ang);
+    const float l1 = ACCURATE ? log_unif_accurate(w.x) : __logf(unif_f(w.x));
+    const float l3 = ACCURATE ? log_unif_accurate(w.z) : __logf(unif_f(w.z));
+    X = -(l1 + cs * cs * l3) * ia;
     const float u4 = unif_f(w.w);
     if (u4 * u4 <= 1.0f - 0.5f * X) {
       acc = true;
@@ -494,6 +503,19 @@ __device__ __forceinline__ bool su2_draw(float alpha, int hits, uint2 key, uint3
   x[2] = rho * sinth * sphi;
   x[3] = rho * costh;
   return true;
+}
+
+__device__ __forceinline__ bool su2_draw(float alpha, int hits, uint2 key, uint32_t c0, uint32_t c1, uint32_t tag,
+                                         float x[4], uint32_t &nprop) {
+  if (alpha >= kAlphaFp64) {
+    double xd[4];
+    const bool a = su2_draw_d((double)alpha, hits, key, c0, c1, tag, xd, nprop);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = (float)xd[i];
+    return a;
+  }
+  if (alpha < kAlphaAccurateLog) return su2_draw_f<true>(alpha, hits, key, c0, c1, tag, x, nprop);
+  return su2_draw_f<false>(alpha, hits, key, c0, c1, tag, x, nprop);
 }
 
 // ------------------------------------------------------------------ Cabibbo-Marinari

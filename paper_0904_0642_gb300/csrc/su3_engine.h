@@ -29,6 +29,10 @@ constexpr uint32_t kHitDirection = 255u;
 // where X ~ 1/alpha is small and its relative precision sets the size of
 // the rotation).
 constexpr float kAlphaFp64 = 32.0f;
+// FP32 storage: below this alpha (strong coupling) the float draw takes the
+// accurate logf / cosf instead of their SFU forms (their absolute errors
+// would be divided by alpha).
+constexpr float kAlphaAccurateLog = 2.0f;
 
 // Results per measurement slot: [total, space, time, poly_re, poly_im].
 constexpr int kMeasVals = 5;

@@ -52,6 +52,10 @@ def test_version_and_defaults():
     (dict(boundary=3), "boundary"),
     (dict(rng_period=[3, 4, 4, 4]), "rng_period"),
     (dict(glue_mask=1 << 4), "glue_mask"),
+    (dict(hits=255), "hits"),
+    (dict(beta1=float("inf")), "beta1"),
+    (dict(reunit_every=-1), "negative"),
+    (dict(dims=[256, 256, 256, 64]), "too large"),  # 2^30 sites: link storage beyond 2^31 vectors
 ])
 def test_invalid_configs_are_rejected(change, msg):
     kw = dict(dims=[4, 4, 4, 4])

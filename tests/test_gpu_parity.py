@@ -72,17 +72,24 @@ def test_set_get_round_trip(storage, tol):
         assert np.max(np.abs(lat.get_links() - o.U)) <= tol
 
 
-def _sensitivity(make, start, **sweep_kw):
-    """Each link's response, in the oracle, to a perturbation of the start at
+def _sensitivity(make, start, samples=4, **sweep_kw):
+    """Each link's response, in the oracle, to perturbations of the start at
     float rounding level (every element times 1 + 2^-24 r, r uniform in
-    [-1, 1]): the empirical condition of the one-sweep update."""
+    [-1, 1]): the empirical condition of the one-sweep update, the largest
+    response over `samples` independent perturbations (one perturbation can
+    miss the sensitive direction: at beta = 0.3 with 254 hits single samples
+    differ from the largest of eight by up to a factor 16)."""
     rng = np.random.default_rng(99)
-    a, b = make(), make()
+    a = make()
     a.U[...] = start
-    b.U[...] = start * (1 + 2.0 ** -24 * rng.uniform(-1, 1, start.shape))
     a.sweep(**sweep_kw)
-    b.sweep(**sweep_kw)
-    return np.max(np.abs(a.U - b.U).reshape(-1, 18), axis=1)
+    out = np.zeros(a.U.size // 18)
+    for _ in range(samples):
+        b = make()
+        b.U[...] = start * (1 + 2.0 ** -24 * rng.uniform(-1, 1, start.shape))
+        b.sweep(**sweep_kw)
+        out = np.maximum(out, np.max(np.abs(a.U - b.U).reshape(-1, 18), axis=1))
+    return out
 
 
 def _flip_check(got, want, margins, sens, tol):
