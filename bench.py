@@ -270,6 +270,37 @@ def bench_divided(su3, torch, stream):
             "ratio": out["2x2x2x2"] / out["undivided"]}
 
 
+def bench_fp32_18(su3, torch, stream, peaks):
+    """The 32^4 workload with all 18 reals of every link stored in float (72
+    bytes a link instead of 48: row 3 is loaded, not rebuilt): throughput of
+    the step and of the update kernel against the HBM peak, with its own
+    algorithmic bytes (2D + 1) x 72 per update."""
+    lat = su3.Lattice(DIMS, beta=BETA, seed=SEED, hits=HITS, storage=su3.SU3_FP32_18, start=su3.SU3_START_HOT,
+                      reunit_every=SWEEPS_PER_STEP, measure_every=SWEEPS_PER_STEP, stream=stream)
+    var, thr, ctas, _ = lat.autotune()
+    lat.sweep(SWEEPS_PER_STEP)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        lat.sweep(SWEEPS_PER_STEP)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    value = 3 * SWEEPS_PER_STEP * lat.nlinks / (e0.elapsed_time(e1) * 1e-3)
+    lat.set_profiling(True)
+    lat.profile(reset=True)
+    lat.sweep(SWEEPS_PER_STEP)
+    prof = lat.profile(reset=True)
+    upd_us = 1e3 * prof["update_ms"] / max(1, prof["update_launches"])
+    alg = (lat.nlinks // len(DIMS) // 2) * (2 * len(DIMS) + 1) * 72
+    plaq = lat.plaquette()[0]
+    lat.close()
+    return {"workload": "32^4 PBC beta=6 hot start, FP32 18-real storage, 10 sweeps + re-unitarisation per step",
+            "value": value, "unit": UNIT, "update_us": upd_us, "alg_bytes_per_update_launch": alg,
+            "hbm_frac": alg / (upd_us * 1e-6) / 1e9 / peaks["hbm_gbs"], "plaquette": plaq,
+            "launch": {"variant": var, "threads": thr, "ctas_per_sm": ctas}}
+
+
 def bench_dlt_and_d3(su3, torch, stream):
     out = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -529,6 +560,7 @@ def main():
         lat64.close()
         if rank == 0 and world == 1:
             line["ensemble_256x8^4"] = bench_ensemble(su3, torch, stream)
+            line["fp32_18_32^4"] = bench_fp32_18(su3, torch, stream, peaks)
             line["divided_32^4_2x2x2x2"] = bench_divided(su3, torch, stream)
             line.update(bench_dlt_and_d3(su3, torch, stream))
             line["serving"] = bench_serving(su3, torch)

@@ -52,9 +52,13 @@ typedef enum {
 
 typedef enum { SU3_PBC = 0, SU3_DLT = 1 } su3_boundary;
 
-/* Device link storage.  FP64_18: all 18 reals in double.  FP32_12: the first
- * two rows in float, the third rebuilt as conj(row1 x row2) on load. */
-typedef enum { SU3_FP64_18 = 0, SU3_FP32_12 = 1 } su3_storage;
+/* Device link storage.  FP64_18: all 18 reals in double (144 bytes per
+ * link).  FP32_12: the first two rows in float, the third rebuilt as
+ * conj(row1 x row2) on load (48 bytes).  FP32_18: all 18 reals in float
+ * (72 bytes; the third row is loaded, not rebuilt, and is renewed by
+ * re-unitarisation).  Both float forms draw and update in float (Sec. 2.1:
+ * the FHKP draw switches to double for alpha >= 32). */
+typedef enum { SU3_FP64_18 = 0, SU3_FP32_12 = 1, SU3_FP32_18 = 2 } su3_storage;
 
 typedef enum { SU3_START_COLD = 0, SU3_START_HOT = 1 } su3_start;
 
@@ -169,7 +173,8 @@ su3_status su3_measurement_latest(su3_lattice *lat, double *host_out, size_t n);
 
 /* Copy all links to / from the host in the canonical layout; n is the
  * number of doubles in the host buffer (>= 18 * links).  set_links rounds
- * to the storage precision (FP32_12 keeps rows 1 and 2).  Synchronous. */
+ * to the storage precision (FP32_12 keeps rows 1 and 2, FP32_18 rounds all
+ * 18 reals to float).  Synchronous. */
 su3_status su3_get_links(su3_lattice *lat, double *host, size_t n);
 su3_status su3_set_links(su3_lattice *lat, const double *host, size_t n);
 
@@ -223,10 +228,11 @@ su3_status su3_set_sweep_counter(su3_lattice *lat, uint64_t sweeps);
 /* Number of links (D*V*layers) and device bytes of the link storage. */
 su3_status su3_lattice_info(su3_lattice *lat, size_t *links, size_t *bytes);
 
-/* Launch shape.  variant: register variant of the update kernel (FP32
+/* Launch shape.  variant: register variant of the update kernel (FP32_12
  * storage: 0 = 128 registers / up to 256 threads, 1 = 96 / up to 128,
  * 2 = 96 / up to 128, 3 = 128 / up to 256 and 4 = 85 / up to 256 with the
- * loop over staple directions kept rolled; FP64 storage: 0 only).  threads:
+ * loop over staple directions kept rolled; FP32_18 and FP64 storage: 0
+ * only).  threads:
  * CTA width, a multiple of 32 up to the variant's maximum.  ctas_per_sm = 0
  * launches one CTA per tile of `threads` sites; > 0 a persistent grid of
  * (SM count x ctas_per_sm) CTAs that loop over the tiles.  The random

@@ -28,7 +28,7 @@ MAX_D = 4
 
 SU3_OK, SU3_EINVAL, SU3_ENOMEM, SU3_ECUDA, SU3_ETIMEOUT, SU3_EBUSY, SU3_ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
 SU3_PBC, SU3_DLT = 0, 1
-SU3_FP64_18, SU3_FP32_12 = 0, 1
+SU3_FP64_18, SU3_FP32_12, SU3_FP32_18 = 0, 1, 2
 SU3_START_COLD, SU3_START_HOT = 0, 1
 SU3_LINKS_FP64_18, SU3_LINKS_FP32_12 = 0, 1
 

@@ -86,11 +86,12 @@ static su3_status validate(const su3_config *c) {
   const int layers = c->boundary == SU3_DLT ? 2 : 1;
   if (c->boundary != SU3_PBC && c->boundary != SU3_DLT) return fail(SU3_EINVAL, "unknown boundary %d", c->boundary);
   if (V * layers * c->D * 9 >= 0x7fffffffLL)
-    return fail(SU3_EINVAL, "lattice too large: link storage must stay below 2^31 16-byte vectors");
+    return fail(SU3_EINVAL, "lattice too large: link storage must stay below 2^31 vectors");
   if (!(c->beta >= 0.0) || !std::isfinite(c->beta)) return fail(SU3_EINVAL, "beta=%g must be finite and >= 0", c->beta);
   if (!std::isfinite(c->beta1)) return fail(SU3_EINVAL, "beta1=%g must be finite (< 0: equal to beta)", c->beta1);
   if (c->hits < 1 || c->hits > 254) return fail(SU3_EINVAL, "hits=%d outside 1..254", c->hits);
-  if (c->storage != SU3_FP64_18 && c->storage != SU3_FP32_12) return fail(SU3_EINVAL, "unknown storage %d", c->storage);
+  if (c->storage != SU3_FP64_18 && c->storage != SU3_FP32_12 && c->storage != SU3_FP32_18)
+    return fail(SU3_EINVAL, "unknown storage %d", c->storage);
   if (c->start != SU3_START_COLD && c->start != SU3_START_HOT) return fail(SU3_EINVAL, "unknown start %d", c->start);
   if (c->reunit_every < 0 || c->measure_every < 0 || c->measure_capacity < 0)
     return fail(SU3_EINVAL, "negative cadence or capacity");
@@ -118,7 +119,7 @@ static su3_status validate(const su3_config *c) {
     }
   }
   if (Vbox * layers * c->D * 9 >= 0x7fffffffLL)
-    return fail(SU3_EINVAL, "divided lattice too large: its boxes must stay below 2^31 16-byte vectors");
+    return fail(SU3_EINVAL, "divided lattice too large: its boxes must stay below 2^31 vectors");
   return SU3_OK;
 }
 
@@ -128,13 +129,15 @@ static bool divided(const su3_config *c) {
   return false;
 }
 
-static int nq_of(int storage) { return storage == SU3_FP64_18 ? 9 : 3; }
+static size_t bytes_per_link(int storage) {
+  return storage == SU3_FP64_18 ? 144 : (storage == SU3_FP32_18 ? 72 : 48);
+}
 
 static size_t link_bytes_of(const su3_config *c) {
   size_t V = 1;
   for (int i = 0; i < c->D; ++i) V *= (size_t)c->dims[i];
   const int layers = c->boundary == SU3_DLT ? 2 : 1;
-  return (size_t)layers * c->D * V * nq_of(c->storage) * 16;
+  return (size_t)layers * c->D * V * bytes_per_link(c->storage);
 }
 
 // Bytes of the sublattice boxes of a divided lattice (interiors and halos).
@@ -146,7 +149,7 @@ static size_t box_bytes_of(const su3_config *c) {
     Vpad *= (size_t)(c->dims[i] / k + (k > 1 ? 2 : 0));
   }
   const int layers = c->boundary == SU3_DLT ? 2 : 1;
-  return (size_t)layers * c->D * nb * Vpad * nq_of(c->storage) * 16;
+  return (size_t)layers * c->D * nb * Vpad * bytes_per_link(c->storage);
 }
 
 extern "C" size_t su3_link_bytes(const su3_config *c) {

@@ -288,10 +288,14 @@ __device__ __forceinline__ void acc_su3_2rows_w(M3<R> &A, const M3<R> &m, R w) {
 // of consecutive sites reads each q-vector as one contiguous 512-byte line
 // of 128-bit loads.
 
+// Every form has load (3 rows), load2 (rows 1, 2; row 3 left unset), store
+// and copy (one link between two planes, for halo and box copies).
+
 struct StoreF32x12 {
   using R = float;
   using Vec = float4;
   static constexpr int NQ = 3;  // rows 1, 2: six complex numbers
+  static constexpr bool kTwoRows = true;
   // rows 0, 1 only (row 2 left unset)
   __device__ static __forceinline__ M3<float> load2(const Vec *plane, int Vh, int jj) {
     const Vec *p = plane + jj;
@@ -316,12 +320,67 @@ struct StoreF32x12 {
     p[Vh] = make_float4(m.e[0][2].re, m.e[0][2].im, m.e[1][0].re, m.e[1][0].im);
     p[2 * Vh] = make_float4(m.e[1][1].re, m.e[1][1].im, m.e[1][2].re, m.e[1][2].im);
   }
+  __device__ static __forceinline__ void copy(Vec *dst, int dVh, int dj, const Vec *src, int sVh, int sj) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) dst[(size_t)q * dVh + dj] = src[(size_t)q * sVh + sj];
+  }
+};
+
+// All 18 reals in float: the 12-real planes (rows 1, 2 as three 128-bit
+// vectors) followed by row 3 as one 128-bit and one 64-bit vector.  In units
+// of Vec = float2 a (layer, colour, mu) plane group spans 9 Vh: float4 plane
+// k (k = 0..3) starts at 2 k Vh, the float2 plane at 8 Vh.  Plane groups
+// start on 16-byte boundaries because Vh is even (all extents are even).
+// Loads of rows 1, 2 are those of the 12-real form; row 3 costs two more
+// loads instead of the cross product.
+struct StoreF32x18 {
+  using R = float;
+  using Vec = float2;
+  static constexpr int NQ = 9;  // float2 units per link
+  static constexpr bool kTwoRows = false;
+  __device__ static __forceinline__ M3<float> load2(const Vec *plane, int Vh, int jj) {
+    const float4 *p = reinterpret_cast<const float4 *>(plane) + jj;
+    const float4 q0 = __ldg(p), q1 = __ldg(p + Vh), q2 = __ldg(p + 2 * Vh);
+    M3<float> m;
+    m.e[0][0] = {q0.x, q0.y};
+    m.e[0][1] = {q0.z, q0.w};
+    m.e[0][2] = {q1.x, q1.y};
+    m.e[1][0] = {q1.z, q1.w};
+    m.e[1][1] = {q2.x, q2.y};
+    m.e[1][2] = {q2.z, q2.w};
+    return m;
+  }
+  __device__ static __forceinline__ M3<float> load(const Vec *plane, int Vh, int jj) {
+    M3<float> m = load2(plane, Vh, jj);
+    const float4 q3 = __ldg(reinterpret_cast<const float4 *>(plane) + 3 * Vh + jj);
+    const float2 q4 = __ldg(plane + 8 * Vh + jj);
+    m.e[2][0] = {q3.x, q3.y};
+    m.e[2][1] = {q3.z, q3.w};
+    m.e[2][2] = {q4.x, q4.y};
+    return m;
+  }
+  __device__ static __forceinline__ void store(Vec *plane, int Vh, int jj, const M3<float> &m) {
+    float4 *p = reinterpret_cast<float4 *>(plane) + jj;
+    p[0] = make_float4(m.e[0][0].re, m.e[0][0].im, m.e[0][1].re, m.e[0][1].im);
+    p[Vh] = make_float4(m.e[0][2].re, m.e[0][2].im, m.e[1][0].re, m.e[1][0].im);
+    p[2 * Vh] = make_float4(m.e[1][1].re, m.e[1][1].im, m.e[1][2].re, m.e[1][2].im);
+    p[3 * Vh] = make_float4(m.e[2][0].re, m.e[2][0].im, m.e[2][1].re, m.e[2][1].im);
+    plane[8 * Vh + jj] = make_float2(m.e[2][2].re, m.e[2][2].im);
+  }
+  __device__ static __forceinline__ void copy(Vec *dst, int dVh, int dj, const Vec *src, int sVh, int sj) {
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d4[(size_t)k * dVh + dj] = s4[(size_t)k * sVh + sj];
+    dst[(size_t)8 * dVh + dj] = src[(size_t)8 * sVh + sj];
+  }
 };
 
 struct StoreF64x18 {
   using R = double;
   using Vec = double2;
   static constexpr int NQ = 9;  // one complex number per 128-bit vector
+  static constexpr bool kTwoRows = false;
   __device__ static __forceinline__ M3<double> load(const Vec *plane, int Vh, int jj) {
     const Vec *p = plane + jj;
     M3<double> m;
@@ -346,6 +405,10 @@ struct StoreF64x18 {
     Vec *p = plane + jj;
 #pragma unroll
     for (int q = 0; q < 9; ++q) p[q * Vh] = make_double2(m.e[q / 3][q % 3].re, m.e[q / 3][q % 3].im);
+  }
+  __device__ static __forceinline__ void copy(Vec *dst, int dVh, int dj, const Vec *src, int sVh, int sj) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) dst[(size_t)q * dVh + dj] = src[(size_t)q * sVh + sj];
   }
 };
 

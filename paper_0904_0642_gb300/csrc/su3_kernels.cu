@@ -267,8 +267,8 @@ __device__ __forceinline__ M3<double> load_rows2_d(const typename S::Vec *p, int
 // Two links per step: their Gram-Schmidt chains are independent.
 template <class S, bool SUB = false>
 __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int jj) {
-  constexpr bool kTwoRows = sizeof(typename S::R) == 4;  // FP32 storage keeps rows 1, 2 only
-  constexpr int kNewton = kTwoRows ? 1 : 2;
+  constexpr bool kTwoRows = S::kTwoRows;  // the 12-real form keeps rows 1, 2 only
+  constexpr int kNewton = sizeof(typename S::R) == 4 ? 1 : 2;  // float storage: one Newton step suffices
   const int Vh = d.Vh;
   for (int colour = 0; colour < 2; ++colour) {
     const int js = SUB ? (site_of<true>(d, layer, colour, jj).s >> 1) : jj;
@@ -816,12 +816,8 @@ __global__ void k_halo(const ChainDesc *desc_dev, const ChainState *state_dev, i
         bmul *= d.bdiv[k];
       }
     const int vsrc = (L ^ flip) * d.nb + bsrc;
-    for (int mu = m0; mu < m1; ++mu) {
-      typename S::Vec *dst = plane_ptr<S>(d, vl, colour, mu) + (h.x >> 1);
-      const typename S::Vec *src = plane_ptr<S>(d, vsrc, colour, mu) + (h.y >> 1);
-#pragma unroll
-      for (int q = 0; q < S::NQ; ++q) dst[(size_t)q * d.Vh] = src[(size_t)q * d.Vh];
-    }
+    for (int mu = m0; mu < m1; ++mu)
+      S::copy(plane_ptr<S>(d, vl, colour, mu), d.Vh, h.x >> 1, plane_ptr<S>(d, vsrc, colour, mu), d.Vh, h.y >> 1);
   }
 }
 
@@ -848,15 +844,12 @@ __global__ void k_sub_copy(const ChainDesc *sub_dev, const ChainDesc *plain_dev,
       sp += (gx - bo * d.idims[k] + d.hpad[k]) * d.stride[k];
     }
     const int colour = par & 1;
-    typename S::Vec *pv = plane_ptr<S>(p, L, colour, mu) + (s >> 1);
-    typename S::Vec *sv = plane_ptr<S>(d, L * d.nb + b, colour, mu) + (sp >> 1);
-#pragma unroll
-    for (int q = 0; q < S::NQ; ++q) {
-      if (to_sub)
-        sv[(size_t)q * d.Vh] = pv[(size_t)q * p.Vh];
-      else
-        pv[(size_t)q * p.Vh] = sv[(size_t)q * d.Vh];
-    }
+    typename S::Vec *pv = plane_ptr<S>(p, L, colour, mu);
+    typename S::Vec *sv = plane_ptr<S>(d, L * d.nb + b, colour, mu);
+    if (to_sub)
+      S::copy(sv, d.Vh, sp >> 1, pv, p.Vh, s >> 1);
+    else
+      S::copy(pv, p.Vh, s >> 1, sv, d.Vh, sp >> 1);
   }
 }
 
@@ -944,47 +937,53 @@ static cudaError_t noalloc_scratch(double **ptr) {
   return cudaSuccess;
 }
 
+// Run f with a value of the storage form of `storage` (0: FP64 18-real,
+// 1: FP32 12-real, 2: FP32 18-real); f launches the kernels of that form.
+template <class F>
+static cudaError_t by_storage(int storage, F &&f) {
+  switch (storage) {
+    case 0: return f(StoreF64x18{});
+    case 2: return f(StoreF32x18{});
+    default: return f(StoreF32x12{});
+  }
+}
+
 cudaError_t launch_measure_noalloc(int storage, const ChainDesc &d, int block, double *out, cudaStream_t st) {
   double *partials = nullptr;
   cudaError_t e = noalloc_scratch(&partials);
   if (e != cudaSuccess) return e;
   const int tiles = d.tiles_per_layer * d.nlayers;
   const int grid = tiles < 4096 ? tiles : 4096;
-  if (storage == 0)
-    k_measure_noalloc<StoreF64x18><<<grid, block, 0, st>>>(d, partials);
-  else
-    k_measure_noalloc<StoreF32x12><<<grid, block, 0, st>>>(d, partials);
-  k_measure_finalize_noalloc<<<1, 32, 0, st>>>(d, partials, out);
-  return cudaGetLastError();
+  return by_storage(storage, [&](auto s) {
+    k_measure_noalloc<decltype(s)><<<grid, block, 0, st>>>(d, partials);
+    k_measure_finalize_noalloc<<<1, 32, 0, st>>>(d, partials, out);
+    return cudaGetLastError();
+  });
 }
 
 // ------------------------------------------------------------------ launchers
+// Tick kernel forms: FP32 12-real has variants 0..4 (TickBounds), FP32
+// 18-real variant 0 only, FP64 its one form (10).  A chain divided into
+// sublattice boxes runs one form: FP32 the rolled 128-register variant (3).
 
-int tick_variants(int storage) { return storage == 0 ? 1 : 5; }
+constexpr int kSubVariant = 3;
 
-template <int V, bool WT, bool SUB = false>
+int tick_variants(int storage) { return storage == 1 ? 5 : 1; }
+
+template <class S, int V, bool WT, bool SUB = false>
 static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_t st) {
-  if constexpr (V == 10)
-    k_tick<StoreF64x18, 10, WT, SUB><<<grid, block, 0, st>>>(ea);
-  else
-    k_tick<StoreF32x12, V, WT, SUB><<<grid, block, 0, st>>>(ea);
+  k_tick<S, V, WT, SUB><<<grid, block, 0, st>>>(ea);
   return cudaGetLastError();
 }
 
-template <int V, bool WT, bool SUB = false>
+template <class S, int V, bool WT, bool SUB = false>
 static cudaError_t occ_v(int block, int *ctas) {
-  if constexpr (V == 10)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF64x18, 10, WT, SUB>, block, 0);
-  else
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<StoreF32x12, V, WT, SUB>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<S, V, WT, SUB>, block, 0);
 }
-
-// A chain divided into sublattice boxes runs one kernel form: FP32 the
-// rolled 128-register variant (3), FP64 its only one.
-constexpr int kSubVariant = 3;
 
 int tick_max_threads(int storage, int variant) {
   if (storage == 0) return TickBounds<10>::kThreads;
+  if (storage == 2) return TickBounds<0>::kThreads;
   switch (variant) {
     case 0: return TickBounds<0>::kThreads;
     case 1: return TickBounds<1>::kThreads;
@@ -994,26 +993,41 @@ int tick_max_threads(int storage, int variant) {
   }
 }
 
-template <bool WT>
-static cudaError_t launch_tick_w(int storage, int variant, bool sub, const EngineArgs &ea, int grid, int block,
-                                 cudaStream_t st) {
-  if (sub) return storage == 0 ? tick_v<10, WT, true>(ea, grid, block, st) : tick_v<kSubVariant, WT, true>(ea, grid, block, st);
-  if (storage == 0) return tick_v<10, WT>(ea, grid, block, st);
+// One switch for launching and for occupancy queries: OP<S, V, WT, SUB>.
+template <template <class, int, bool, bool> class OP, bool WT, class... A>
+static cudaError_t tick_dispatch(int storage, int variant, bool sub, A... a) {
+  if (storage == 0) return sub ? OP<StoreF64x18, 10, WT, true>::run(a...) : OP<StoreF64x18, 10, WT, false>::run(a...);
+  if (storage == 2)
+    return sub ? OP<StoreF32x18, kSubVariant, WT, true>::run(a...) : OP<StoreF32x18, 0, WT, false>::run(a...);
+  if (sub) return OP<StoreF32x12, kSubVariant, WT, true>::run(a...);
   switch (variant) {
-    case 0: return tick_v<0, WT>(ea, grid, block, st);
-    case 1: return tick_v<1, WT>(ea, grid, block, st);
-    case 2: return tick_v<2, WT>(ea, grid, block, st);
-    case 3: return tick_v<3, WT>(ea, grid, block, st);
-    default: return tick_v<4, WT>(ea, grid, block, st);
+    case 0: return OP<StoreF32x12, 0, WT, false>::run(a...);
+    case 1: return OP<StoreF32x12, 1, WT, false>::run(a...);
+    case 2: return OP<StoreF32x12, 2, WT, false>::run(a...);
+    case 3: return OP<StoreF32x12, 3, WT, false>::run(a...);
+    default: return OP<StoreF32x12, 4, WT, false>::run(a...);
   }
 }
+
+template <class S, int V, bool WT, bool SUB>
+struct TickLaunch {
+  static cudaError_t run(const EngineArgs *ea, int grid, int block, cudaStream_t st) {
+    return tick_v<S, V, WT, SUB>(*ea, grid, block, st);
+  }
+};
+
+template <class S, int V, bool WT, bool SUB>
+struct TickOccupancy {
+  static cudaError_t run(int block, int *ctas) { return occ_v<S, V, WT, SUB>(block, ctas); }
+};
 
 cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, const EngineArgs &ea, int grid, int block,
                         cudaStream_t st) {
   if (sub) variant = storage == 0 ? 0 : kSubVariant;
   if (block > tick_max_threads(storage, variant)) return cudaErrorInvalidConfiguration;
-  return weighted ? launch_tick_w<true>(storage, variant, sub, ea, grid, block, st)
-                  : launch_tick_w<false>(storage, variant, sub, ea, grid, block, st);
+  const EngineArgs *pa = &ea;
+  return weighted ? tick_dispatch<TickLaunch, true>(storage, variant, sub, pa, grid, block, st)
+                  : tick_dispatch<TickLaunch, false>(storage, variant, sub, pa, grid, block, st);
 }
 
 cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, int all, int boxes,
@@ -1021,84 +1035,65 @@ cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState
   const int block = 256;
   const dim3 grid((unsigned)((halo_sites + block - 1) / block > 0 ? (halo_sites + block - 1) / block : 1),
                   (unsigned)boxes);
-  if (storage == 0)
-    k_halo<StoreF64x18><<<grid, block, 0, st>>>(desc_dev, state_dev, all);
-  else
-    k_halo<StoreF32x12><<<grid, block, 0, st>>>(desc_dev, state_dev, all);
-  return cudaGetLastError();
+  return by_storage(storage, [&](auto s) {
+    k_halo<decltype(s)><<<grid, block, 0, st>>>(desc_dev, state_dev, all);
+    return cudaGetLastError();
+  });
+}
+
+static int copy_grid(size_t nlinks, int block) {
+  return (int)((nlinks + block - 1) / block < 65536 ? (nlinks + block - 1) / block : 65536);
 }
 
 cudaError_t launch_sub_copy(int storage, const ChainDesc *sub_dev, const ChainDesc *plain_dev, size_t nlinks,
                             int to_sub, cudaStream_t st) {
-  const int block = 256;
-  const int grid = (int)((nlinks + block - 1) / block < 65536 ? (nlinks + block - 1) / block : 65536);
-  if (storage == 0)
-    k_sub_copy<StoreF64x18><<<grid, block, 0, st>>>(sub_dev, plain_dev, to_sub);
-  else
-    k_sub_copy<StoreF32x12><<<grid, block, 0, st>>>(sub_dev, plain_dev, to_sub);
-  return cudaGetLastError();
+  const int block = 256, grid = copy_grid(nlinks, block);
+  return by_storage(storage, [&](auto s) {
+    k_sub_copy<decltype(s)><<<grid, block, 0, st>>>(sub_dev, plain_dev, to_sub);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st) {
   const int grid = tiles_total < 4096 ? tiles_total : 4096;
-  if (storage == 0)
-    k_measure<StoreF64x18><<<grid, block, 0, st>>>(desc_dev);
-  else
-    k_measure<StoreF32x12><<<grid, block, 0, st>>>(desc_dev);
-  k_measure_finalize<<<1, 32, 0, st>>>(desc_dev, out);
-  return cudaGetLastError();
+  return by_storage(storage, [&](auto s) {
+    k_measure<decltype(s)><<<grid, block, 0, st>>>(desc_dev);
+    k_measure_finalize<<<1, 32, 0, st>>>(desc_dev, out);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_start(int storage, ChainDesc *desc_dev, size_t nlinks, int hot, cudaStream_t st) {
-  const int block = 256;
-  const int grid = (int)((nlinks + block - 1) / block < 65536 ? (nlinks + block - 1) / block : 65536);
-  if (storage == 0)
-    k_start<StoreF64x18><<<grid, block, 0, st>>>(desc_dev, hot);
-  else
-    k_start<StoreF32x12><<<grid, block, 0, st>>>(desc_dev, hot);
-  return cudaGetLastError();
+  const int block = 256, grid = copy_grid(nlinks, block);
+  return by_storage(storage, [&](auto s) {
+    k_start<decltype(s)><<<grid, block, 0, st>>>(desc_dev, hot);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_convert_rows2(int storage, ChainDesc *desc_dev, size_t nlinks, const float *src, cudaStream_t st) {
-  const int block = 256;
-  const int grid = (int)((nlinks + block - 1) / block < 65536 ? (nlinks + block - 1) / block : 65536);
-  if (storage == 0)
-    k_convert_rows2<StoreF64x18><<<grid, block, 0, st>>>(desc_dev, src);
-  else
-    k_convert_rows2<StoreF32x12><<<grid, block, 0, st>>>(desc_dev, src);
-  return cudaGetLastError();
+  const int block = 256, grid = copy_grid(nlinks, block);
+  return by_storage(storage, [&](auto s) {
+    k_convert_rows2<decltype(s)><<<grid, block, 0, st>>>(desc_dev, src);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, double *canon, int to_canonical,
                            cudaStream_t st) {
-  const int block = 256;
-  const int grid = (int)((nlinks + block - 1) / block < 65536 ? (nlinks + block - 1) / block : 65536);
-  if (storage == 0)
-    k_convert<StoreF64x18><<<grid, block, 0, st>>>(desc_dev, canon, to_canonical);
-  else
-    k_convert<StoreF32x12><<<grid, block, 0, st>>>(desc_dev, canon, to_canonical);
-  return cudaGetLastError();
-}
-
-template <bool WT>
-static cudaError_t tick_occupancy_w(int storage, int variant, bool sub, int block, int *ctas_per_sm) {
-  if (sub) return storage == 0 ? occ_v<10, WT, true>(block, ctas_per_sm) : occ_v<kSubVariant, WT, true>(block, ctas_per_sm);
-  if (storage == 0) return occ_v<10, WT>(block, ctas_per_sm);
-  switch (variant) {
-    case 0: return occ_v<0, WT>(block, ctas_per_sm);
-    case 1: return occ_v<1, WT>(block, ctas_per_sm);
-    case 2: return occ_v<2, WT>(block, ctas_per_sm);
-    case 3: return occ_v<3, WT>(block, ctas_per_sm);
-    default: return occ_v<4, WT>(block, ctas_per_sm);
-  }
+  const int block = 256, grid = copy_grid(nlinks, block);
+  return by_storage(storage, [&](auto s) {
+    k_convert<decltype(s)><<<grid, block, 0, st>>>(desc_dev, canon, to_canonical);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t tick_occupancy(int storage, int variant, bool weighted, bool sub, int block, int *ctas_per_sm) {
   *ctas_per_sm = 0;
   if (sub) variant = storage == 0 ? 0 : kSubVariant;
   if (block > tick_max_threads(storage, variant)) return cudaSuccess;
-  return weighted ? tick_occupancy_w<true>(storage, variant, sub, block, ctas_per_sm)
-                  : tick_occupancy_w<false>(storage, variant, sub, block, ctas_per_sm);
+  return weighted ? tick_dispatch<TickOccupancy, true>(storage, variant, sub, block, ctas_per_sm)
+                  : tick_dispatch<TickOccupancy, false>(storage, variant, sub, block, ctas_per_sm);
 }
 
 void host_advance_stage(const ChainDesc &d, ChainState &s) { advance_stage(d, s); }

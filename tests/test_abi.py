@@ -38,6 +38,9 @@ def test_version_and_defaults():
     assert su3.su3_link_bytes(c) == 4 ** 4 * 4 * 144
     c.storage = su3.SU3_FP32_12
     assert su3.su3_link_bytes(c) == 4 ** 4 * 4 * 48
+    c.storage = su3.SU3_FP32_18
+    assert su3.su3_link_bytes(c) == 4 ** 4 * 4 * 72
+    c.storage = su3.SU3_FP32_12
     c.boundary = su3.SU3_DLT
     assert su3.su3_link_bytes(c) == 2 * 4 ** 4 * 4 * 48
 
@@ -49,6 +52,7 @@ def test_version_and_defaults():
     (dict(beta=float("nan")), "beta"),
     (dict(hits=0), "hits"),
     (dict(storage=7), "storage"),
+    (dict(storage=3), "storage"),
     (dict(boundary=3), "boundary"),
     (dict(rng_period=[3, 4, 4, 4]), "rng_period"),
     (dict(glue_mask=1 << 4), "glue_mask"),

@@ -10,7 +10,7 @@ import paper_0904_0642_gb300 as su3
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12])
+@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12, su3.SU3_FP32_18])
 def test_identical_random_numbers_on_sublattices(storage):
     """Sec. 3.1.1: with the random-number site key taken modulo a 4^4
     sublattice, the 8x8x8x4 lattice reproduces the 4^4 run on every tile."""
@@ -55,7 +55,7 @@ def test_time_glued_dlt_is_double_time_torus():
     assert dlt.polyakov(0) == pytest.approx(tor.polyakov(), abs=1e-15)
 
 
-@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12])
+@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12, su3.SU3_FP32_18])
 def test_graph_and_launch_shape_do_not_change_links(storage):
     kw = dict(beta=6.0, seed=21, storage=storage, start=su3.SU3_START_HOT, reunit_every=3)
     dims = [8, 6, 4, 6]
@@ -144,7 +144,7 @@ def test_measurement_stage_records_every_k_sweeps():
     assert np.allclose(m[:, 0], m[:, 1])  # one layer: the layer slot equals the whole lattice
 
 
-@pytest.mark.parametrize("storage,tol", [(su3.SU3_FP64_18, 1e-11), (su3.SU3_FP32_12, 1e-5)])
+@pytest.mark.parametrize("storage,tol", [(su3.SU3_FP64_18, 1e-11), (su3.SU3_FP32_12, 1e-5), (su3.SU3_FP32_18, 1e-5)])
 def test_full_size_sampled_links(storage, tol):
     """32^4, beta = 6, hot start, one sweep at the benchmark's launch shape:
     links of the first phase (colour 0, direction 1) were updated from the

@@ -42,7 +42,10 @@ def oracle_lattice(g, **kw):
     return oracle.Lattice(g["dims"], nlayers=g.get("nlayers", 1), glue_mask=g.get("glue_mask"), **kw)
 
 
-@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12])
+FLOAT_FORMS = [su3.SU3_FP32_12, su3.SU3_FP32_18]
+
+
+@pytest.mark.parametrize("storage", [su3.SU3_FP64_18] + FLOAT_FORMS)
 @pytest.mark.parametrize("g", GEOMS[:1] + GEOMS[5:6])
 def test_cold_start_observables(g, storage):
     with gpu_lattice(g, storage) as lat:
@@ -59,17 +62,21 @@ def test_hot_start_matches_oracle(g):
     o = oracle_lattice(g).hot_start(2024)
     with gpu_lattice(g, su3.SU3_FP64_18, seed=2024, start=su3.SU3_START_HOT) as lat:
         assert np.max(np.abs(lat.get_links() - o.U)) < 1e-13
-    with gpu_lattice(g, su3.SU3_FP32_12, seed=2024, start=su3.SU3_START_HOT) as lat:
-        assert np.max(np.abs(lat.get_links() - o.U)) < 1e-6
+    for storage in FLOAT_FORMS:
+        with gpu_lattice(g, storage, seed=2024, start=su3.SU3_START_HOT) as lat:
+            assert np.max(np.abs(lat.get_links() - o.U)) < 1e-6
 
 
-@pytest.mark.parametrize("storage,tol", [(su3.SU3_FP64_18, 0.0), (su3.SU3_FP32_12, 2e-7)])
+@pytest.mark.parametrize("storage,tol", [(su3.SU3_FP64_18, 0.0), (su3.SU3_FP32_12, 2e-7), (su3.SU3_FP32_18, 0.0)])
 def test_set_get_round_trip(storage, tol):
+    """FP64 keeps every bit; FP32_18 rounds each real to float (compared with
+    numpy's float32 rounding, bit for bit); FP32_12 also rebuilds row 3."""
     g = GEOMS[1]
     o = oracle_lattice(g).hot_start(5)
+    want = o.U.astype(np.float32).astype(np.float64) if storage == su3.SU3_FP32_18 else o.U
     with gpu_lattice(g, storage) as lat:
         lat.set_links(o.U)
-        assert np.max(np.abs(lat.get_links() - o.U)) <= tol
+        assert np.max(np.abs(lat.get_links() - want)) <= tol
 
 
 def _sensitivity(make, start, samples=4, **sweep_kw):
@@ -126,17 +133,18 @@ def test_one_sweep_fp64(g, beta, hits):
     assert sweeps == 1
 
 
+@pytest.mark.parametrize("storage", FLOAT_FORMS)
 @pytest.mark.parametrize("g", GEOMS)
-def test_one_sweep_fp32(g):
+def test_one_sweep_fp32(g, storage):
     o = oracle_lattice(g).hot_start(12)
-    with gpu_lattice(g, su3.SU3_FP32_12, beta=6.0, seed=7, hits=2) as lat:
+    with gpu_lattice(g, storage, beta=6.0, seed=7, hits=2) as lat:
         lat.set_links(o.U)
         start = lat.get_links()  # the float-rounded start both sides use
     o.U[...] = start
     margins = np.full(o.nlinks, np.inf)
     o.sweep(6.0, 2, 7, n=1, margins=margins)
     sens = _sensitivity(lambda: oracle_lattice(g), start, beta=6.0, hits=2, seed=7, n=1)
-    with gpu_lattice(g, su3.SU3_FP32_12, beta=6.0, seed=7, hits=2) as lat:
+    with gpu_lattice(g, storage, beta=6.0, seed=7, hits=2) as lat:
         lat.set_links(start)
         lat.sweep(1)
         got = lat.get_links()
@@ -160,7 +168,7 @@ def test_config1_cold_start_hundred_sweeps_fp64():
     assert max(diffs) < 1e-9, max(diffs)
 
 
-@pytest.mark.parametrize("storage,tol", [(su3.SU3_FP64_18, 1e-13), (su3.SU3_FP32_12, 2e-6)])
+@pytest.mark.parametrize("storage,tol", [(su3.SU3_FP64_18, 1e-13), (su3.SU3_FP32_12, 2e-6), (su3.SU3_FP32_18, 2e-6)])
 @pytest.mark.parametrize("g", GEOMS)
 def test_observables_match_oracle(g, storage, tol):
     o = oracle_lattice(g).hot_start(3)
@@ -173,7 +181,7 @@ def test_observables_match_oracle(g, storage, tol):
             assert abs(lat.polyakov(layer) - o.polyakov(layer)) < tol
 
 
-@pytest.mark.parametrize("storage,tol", [(su3.SU3_FP64_18, 1e-14), (su3.SU3_FP32_12, 1e-6)])
+@pytest.mark.parametrize("storage,tol", [(su3.SU3_FP64_18, 1e-14), (su3.SU3_FP32_12, 1e-6), (su3.SU3_FP32_18, 1e-6)])
 def test_reunitarize_matches_oracle(storage, tol):
     g = GEOMS[1]
     o = oracle_lattice(g).hot_start(4)

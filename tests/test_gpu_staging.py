@@ -10,7 +10,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("storage,ndiv", [(su3.SU3_FP64_18, None), (su3.SU3_FP32_12, None),
-                                          (su3.SU3_FP32_12, [2, 1, 2, 1])])
+                                          (su3.SU3_FP32_12, [2, 1, 2, 1]), (su3.SU3_FP32_18, None),
+                                          (su3.SU3_FP32_18, [2, 1, 2, 1])])
 def test_stage_apply_equals_set_links(storage, ndiv):
     dims = [8, 8, 4, 4]
     l1 = oracle.Lattice(dims).hot_start(41).U.copy()
@@ -79,7 +80,7 @@ def test_staging_errors():
     assert ei.value.status == su3.SU3_EINVAL
 
 
-@pytest.mark.parametrize("storage", [su3.SU3_FP32_12, su3.SU3_FP64_18])
+@pytest.mark.parametrize("storage", [su3.SU3_FP32_12, su3.SU3_FP64_18, su3.SU3_FP32_18])
 def test_two_row_float_input(storage):
     """SU3_LINKS_FP32_12: rows 1, 2 as float, row 3 rebuilt.  For FP32 12-real
     storage this is exactly what set_links stores from the same values."""

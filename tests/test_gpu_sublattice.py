@@ -30,7 +30,7 @@ def pair(case, storage, **kw):
     return su3.Lattice(case["dims"], **base), su3.Lattice(case["dims"], ndiv=case["ndiv"], **base)
 
 
-@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12])
+@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12, su3.SU3_FP32_18])
 @pytest.mark.parametrize("case", CASES)
 def test_divided_lattice_equals_undivided(case, storage):
     plain, div = pair(case, storage, beta=5.8, seed=17, hits=2, reunit_every=2)
@@ -44,7 +44,7 @@ def test_divided_lattice_equals_undivided(case, storage):
         assert div.polyakov(layer) == plain.polyakov(layer)
 
 
-@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12])
+@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12, su3.SU3_FP32_18])
 def test_divided_from_given_links_and_launch_shapes(storage):
     """set_links scatters into the boxes and refills every halo; graphs,
     launch shapes and resuming do not change the result."""
