@@ -183,13 +183,47 @@ __device__ __forceinline__ void acc_su3_2rows(M3<R> &A, const M3<R> &m) {
   }
 }
 
+// ------------------------------------------------------------------ float <-> double by bits
+// On this GPU the FP64 pipe also executes the float <-> double conversion
+// instructions, and in the FP64 stages (re-unitarisation) that pipe is the
+// bottleneck.  These two conversions move the IEEE-754 fields with integer
+// operations instead (sign; exponent rebias 1023 - 127 = 896; mantissa
+// shifted by 52 - 23 = 29 bits), bit for bit the round-to-nearest-even
+// conversions for every normal input.  Subnormal values (below 2^-126 in
+// magnitude) flush to signed zero; infinities and NaNs are preserved.
+
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sg = u & 0x80000000u, a = u & 0x7FFFFFFFu, e = u & 0x7F800000u;
+  uint32_t hi = sg | ((a >> 3) + (896u << 20));
+  hi = e == 0x7F800000u ? (sg | 0x7FF00000u | ((a >> 3) & 0x000FFFFFu)) : hi;
+  hi = e == 0u ? sg : hi;
+  const uint32_t lo = e == 0u ? 0u : (u << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float d2f_bits(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t sg = hi & 0x80000000u, a = hi & 0x7FFFFFFFu;
+  // in range: double exponent 897..1150 (float exponent 1..254); the
+  // 29 dropped mantissa bits decide the rounding, ties to even; a carry
+  // out of the mantissa steps the exponent (to infinity above the range)
+  uint32_t f = ((a - (896u << 20)) << 3) | (lo >> 29);
+  const uint32_t r = lo & 0x1FFFFFFFu;
+  f += (r > 0x10000000u || (r == 0x10000000u && (f & 1u))) ? 1u : 0u;
+  f = a < (897u << 20) ? 0u : f;
+  const bool nan = a > 0x7FF00000u || (a == 0x7FF00000u && lo != 0u);
+  f = a >= (1151u << 20) ? (nan ? 0x7FC00000u : 0x7F800000u) : f;
+  return __uint_as_float(sg | f);
+}
+
 // 1/sqrt(n) in double: a float seed refined by NEWTON Newton steps,
 // y <- y (3 - n y^2) / 2; each roughly squares the relative error
 // (~2e-7 -> ~1e-13 -> rounding level).  One step is ample for links stored
 // in FP32 (rounded to ~6e-8 afterwards), two reach double rounding.
 template <int NEWTON = 2>
 __device__ __forceinline__ double rsqrt_d(double n) {
-  double y = (double)rsqrtf((float)n);
+  double y = f2d_bits(rsqrtf(d2f_bits(n)));
   const double h = 0.5 * n;
 #pragma unroll
   for (int k = 0; k < NEWTON; ++k) y = y * __fma_rn(-h * y, y, 1.5);
@@ -248,6 +282,22 @@ __device__ __forceinline__ void reunit_d(M3<double> &m) {
     r2[k].im *= i2;
   }
   if constexpr (ROW3) third_row(m);
+}
+
+// A double-precision link in the storage precision R (float: by bits).
+template <typename R>
+__device__ __forceinline__ M3<R> to_storage(const M3<double> &b) {
+  M3<R> a;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if constexpr (sizeof(R) == 4)
+        a.e[i][j] = {d2f_bits(b.e[i][j].re), d2f_bits(b.e[i][j].im)};
+      else
+        a.e[i][j] = {b.e[i][j].re, b.e[i][j].im};
+    }
+  return a;
 }
 
 template <typename A, typename B>

@@ -250,6 +250,9 @@ __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, 
 
 // ------------------------------------------------------------------ re-unitarisation
 
+__device__ __forceinline__ double to_double(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double to_double(double x) { return x; }
+
 // Rows 1, 2 of a stored link in double (row 3 is rebuilt by reunit_d, or
 // not kept at all by two-row storage).
 template <class S>
@@ -260,7 +263,7 @@ __device__ __forceinline__ M3<double> load_rows2_d(const typename S::Vec *p, int
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-      m.e[i][j] = i < 2 ? C<double>{(double)f.e[i][j].re, (double)f.e[i][j].im} : C<double>{0.0, 0.0};
+      m.e[i][j] = i < 2 ? C<double>{to_double(f.e[i][j].re), to_double(f.e[i][j].im)} : C<double>{0.0, 0.0};
   return m;
 }
 
@@ -280,14 +283,14 @@ __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int j
       M3<double> m1 = load_rows2_d<S>(p1, Vh, js);
       reunit_d<kNewton, !kTwoRows>(m0);
       reunit_d<kNewton, !kTwoRows>(m1);
-      S::store(p0, Vh, js, m3_cast<typename S::R>(m0));
-      S::store(p1, Vh, js, m3_cast<typename S::R>(m1));
+      S::store(p0, Vh, js, to_storage<typename S::R>(m0));
+      S::store(p1, Vh, js, to_storage<typename S::R>(m1));
     }
     if (mu < d.D) {
       typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
       M3<double> m = load_rows2_d<S>(p, Vh, js);
       reunit_d<kNewton, !kTwoRows>(m);
-      S::store(p, Vh, js, m3_cast<typename S::R>(m));
+      S::store(p, Vh, js, to_storage<typename S::R>(m));
     }
   }
 }
