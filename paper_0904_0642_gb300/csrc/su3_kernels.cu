@@ -300,12 +300,13 @@ __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int j
 // in double: plaquettes split space/time, and Polyakov lines started at
 // x^D = 0 (the line follows the forward time neighbour until it closes).
 
-// (1/3) Re Tr(U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+) = (1/3) sum_ij
-// Re(P_ij conj(Q_ij)) with P = U_mu(x) U_nu(x+mu), Q = U_nu(x) U_mu(x+nu),
-// taken row by row so that few values are live at once.
+// Re Tr(U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+) = sum_ij Re(P_ij
+// conj(Q_ij)) with P = U_mu(x) U_nu(x+mu), Q = U_nu(x) U_mu(x+nu), taken row
+// by row so that few values are live at once; um = U_mu(x) is loaded once
+// by the caller for all nu.  The factor 1/3 is applied to the sums.
 template <class S, bool SUB = false>
 __device__ __forceinline__ double plaquette_at(const ChainDesc &d, const SiteGeo &g, int colour, int mu, int nu,
-                                               int xmu, int xnu) {
+                                               int xmu, int xnu, const M3<typename S::R> &um) {
   using R = typename S::R;
   const int Vh = d.Vh, layer = g.layer, jj = g.s >> 1, oc = colour ^ 1;
   int offp, flp, offn, fln;
@@ -313,7 +314,6 @@ __device__ __forceinline__ double plaquette_at(const ChainDesc &d, const SiteGeo
   step_fwd(d, xnu, nu, offn, fln);
   const M3<R> a = S::load(plane_ptr<S>(d, lflip<SUB>(d, layer, flp), oc, nu), Vh, (g.s + offp) >> 1);  // U_nu(x+mu)
   const M3<R> b = S::load(plane_ptr<S>(d, lflip<SUB>(d, layer, fln), oc, mu), Vh, (g.s + offn) >> 1);  // U_mu(x+nu)
-  const M3<R> um = S::load(plane_ptr<S>(d, layer, colour, mu), Vh, jj);                  // U_mu(x)
   const M3<R> un = S::load(plane_ptr<S>(d, layer, colour, nu), Vh, jj);                  // U_nu(x)
   R tr = R(0);
 #pragma unroll
@@ -331,12 +331,13 @@ __device__ __forceinline__ double plaquette_at(const ChainDesc &d, const SiteGeo
       tr = fm(p.im, q.im, tr);
     }
   }
-  return (double)tr * (1.0 / 3.0);
+  return to_double(tr);
 }
 
 // Per thread: the two sites of checkerboard index jj (both colours).  Sums
-// in double: plaquettes split space/time, and Polyakov lines started at
-// x^D = 0 (the line follows the forward time neighbour until it closes).
+// in double of Re Tr and Tr (the 1/3 is applied by finalize_measure):
+// plaquettes split space/time, and Polyakov lines started at x^D = 0 (the
+// line follows the forward time neighbour until it closes).
 // SUB: plaquettes read the forward halos; a Polyakov line stays inside its
 // sublattice box only when time is undivided, so it is taken only then.
 template <class S, bool SUB = false>
@@ -348,11 +349,12 @@ __device__ __forceinline__ void measure_site(const ChainDesc &d, int layer, int 
   for (int colour = 0; colour < 2; ++colour) {
     const SiteGeo g = site_of<SUB>(d, layer, colour, jj);
 #pragma unroll 1
-    for (int mu = 0; mu < D; ++mu) {
+    for (int mu = 0; mu + 1 < D; ++mu) {
       const int xmu = sel(g.x, mu);
+      const M3<R> um = S::load(plane_ptr<S>(d, layer, colour, mu), Vh, g.s >> 1);  // U_mu(x)
 #pragma unroll 1
       for (int nu = mu + 1; nu < D; ++nu) {
-        const double p = plaquette_at<S, SUB>(d, g, colour, mu, nu, xmu, sel(g.x, nu));
+        const double p = plaquette_at<S, SUB>(d, g, colour, mu, nu, xmu, sel(g.x, nu), um);
         if (nu == D - 1) acc[1] += p; else acc[0] += p;
       }
     }
@@ -372,8 +374,8 @@ __device__ __forceinline__ void measure_site(const ChainDesc &d, int layer, int 
         if (cs == g.s && cl == layer) break;
         P = mul_nn(P, S::load(plane_ptr<S>(d, cl, cc, t), Vh, cs >> 1));
       }
-      acc[2] += (double)(P.e[0][0].re + P.e[1][1].re + P.e[2][2].re) * (1.0 / 3.0);
-      acc[3] += (double)(P.e[0][0].im + P.e[1][1].im + P.e[2][2].im) * (1.0 / 3.0);
+      acc[2] += to_double(P.e[0][0].re + P.e[1][1].re + P.e[2][2].re);
+      acc[3] += to_double(P.e[0][0].im + P.e[1][1].im + P.e[2][2].im);
     }
   }
 }
@@ -408,9 +410,10 @@ __device__ void finalize_measure(const ChainDesc &d, const double *partials, dou
   const int lane = threadIdx.x & 31;
   double whole[kPartVals] = {0, 0, 0, 0};
   const int D = d.D;
-  const double np_s = (double)d.V * (D - 1) * (D - 2) / 2, np_t = (double)d.V * (D - 1);
+  // the partial sums hold Re Tr and Tr: the counts carry the factor 3
+  const double np_s = 3.0 * d.V * (D - 1) * (D - 2) / 2, np_t = 3.0 * d.V * (D - 1);
   // Polyakov lines are not taken inside sublattice boxes with divided time
-  const double nl = d.hpad[D - 1] ? __longlong_as_double(0x7ff8000000000000ll) : (double)d.spatial_per_layer;
+  const double nl = d.hpad[D - 1] ? __longlong_as_double(0x7ff8000000000000ll) : 3.0 * d.spatial_per_layer;
   for (int layer = 0; layer < d.nlayers; ++layer) {
     double v[kPartVals] = {0, 0, 0, 0};
     for (int t = lane; t < d.tiles_per_layer; t += 32)
