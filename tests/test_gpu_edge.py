@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 DIMS = [4, 4, 2, 4]
 
 
-@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12])
+@pytest.mark.parametrize("storage", [su3.SU3_FP64_18, su3.SU3_FP32_12, su3.SU3_FP32_18])
 def test_beta_zero_never_moves_links(storage):
     lat = su3.Lattice(DIMS, beta=0.0, seed=4, storage=storage, start=su3.SU3_START_HOT, hits=3)
     start = lat.get_links()
@@ -52,7 +52,7 @@ def test_extreme_couplings_one_sweep(beta, hits, start):
     U0 = o.U.copy()
     margins = np.full(o.nlinks, np.inf)
     o.sweep(beta, hits, 5, n=1, margins=margins)
-    for storage in (su3.SU3_FP64_18, su3.SU3_FP32_12):
+    for storage in (su3.SU3_FP64_18, su3.SU3_FP32_12, su3.SU3_FP32_18):
         lat = su3.Lattice(DIMS, beta=beta, seed=5, hits=hits, storage=storage)
         lat.set_links(U0)
         lat.sweep(1)
@@ -62,7 +62,7 @@ def test_extreme_couplings_one_sweep(beta, hits, start):
         else:
             probe = su3.Lattice(DIMS, storage=storage)
             probe.set_links(U0)
-            start32 = probe.get_links()  # the float-rounded start (row 3 rebuilt) both sides use
+            start32 = probe.get_links()  # the float-rounded start (12-real: row 3 rebuilt) both sides use
             lat = su3.Lattice(DIMS, beta=beta, seed=5, hits=hits, storage=storage)
             lat.set_links(start32)
             lat.sweep(1)
