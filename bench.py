@@ -491,8 +491,11 @@ def main():
         # configuration from pinned host memory (su3_stage_links_ex on the
         # library's copy stream: the upload of step k+1 runs while step k
         # sweeps), applies it (su3_apply_links), runs the 10 sweeps +
-        # re-unitarisation + measurement, and reads that step's plaquette
-        # and Polyakov loop back (su3_measurement_latest, 80 bytes).  The
+        # re-unitarisation + measurement, and copies that step's plaquette
+        # and Polyakov loop back to pinned host memory
+        # (su3_measurement_latest_async, 80 bytes), which the host reads
+        # while the next step runs; the last step's result is read before
+        # the clock stops.  The
         # input is the two-row FP32 form of the configuration (12 floats per
         # link, the storage format of this workload); the canonical FP64
         # layout (18 doubles per link) is timed the same way beside it.
@@ -506,6 +509,9 @@ def main():
             else:
                 host = torch.empty((links * 18,), dtype=torch.float64, pin_memory=True).numpy()
                 host[:] = canon.reshape(-1)
+            nres = 5 * (lat.nlayers + 1)
+            outs = [torch.empty(nres, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+            evs = [torch.cuda.Event() for _ in range(2)]
             lat.sweep(SWEEPS_PER_STEP)  # warm
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -513,9 +519,17 @@ def main():
             for k in range(k_e2e):
                 lat.apply_links()
                 lat.sweep(SWEEPS_PER_STEP)
+                # the next input first: a copy queued behind this step's
+                # result copy could wait for this step's sweeps
                 if k + 1 < k_e2e:
                     lat.stage_links(host, fmt=fmt)
-                result = lat.latest_measurement()
+                lat.latest_measurement_async(outs[k % 2])  # this step's result, copied in stream order
+                evs[k % 2].record(stream)
+                if k >= 1:  # the previous step's result, read while this step runs
+                    evs[(k - 1) % 2].synchronize()
+                    result = outs[(k - 1) % 2].copy()
+            evs[(k_e2e - 1) % 2].synchronize()
+            result = outs[(k_e2e - 1) % 2].copy()
             t = max_over_ranks(time.perf_counter() - t0)
             # one upload alone (copy + apply + a synchronising read), for its bandwidth
             torch.cuda.synchronize()

@@ -171,6 +171,18 @@ su3_status su3_measurements(su3_lattice *lat, double *host_out, size_t max, size
  * Synchronises. */
 su3_status su3_measurement_latest(su3_lattice *lat, double *host_out, size_t n);
 
+/* The same without waiting: queues the copy of the most recent measurement
+ * recorded by the work queued so far (stream order) into host_out and
+ * returns at once; ENOTFOUND when the queued sweeps record none.  host_out
+ * should be page-locked (else the copy is not asynchronous) and is valid
+ * once the lattice's stream has reached the copy: after su3_synchronize,
+ * or an event the caller records on the stream it passed at creation.  A
+ * pipelined caller reads step k's result while step k+1 runs. */
+su3_status su3_measurement_latest_async(su3_lattice *lat, double *host_out, size_t n);
+
+/* Wait until all work queued on the lattice's stream has finished. */
+su3_status su3_synchronize(su3_lattice *lat);
+
 /* Copy all links to / from the host in the canonical layout; n is the
  * number of doubles in the host buffer (>= 18 * links).  set_links rounds
  * to the storage precision (FP32_12 keeps rows 1 and 2, FP32_18 rounds all

@@ -35,7 +35,7 @@ SU3_LINKS_FP64_18, SU3_LINKS_FP32_12 = 0, 1
 EXPORTED = [
     "su3_config_init", "su3_link_bytes", "su3_lattice_create", "su3_lattice_create_ex", "su3_lattice_destroy",
     "su3_sweep", "su3_reunitarize", "su3_plaquette", "su3_polyakov", "su3_measure_async", "su3_measurements",
-    "su3_get_links", "su3_set_links", "su3_stage_links", "su3_stage_links_ex", "su3_apply_links", "su3_measurement_latest", "su3_stats", "su3_action", "su3_action_reset", "su3_set_sweep_counter", "su3_lattice_info", "su3_set_launch",
+    "su3_get_links", "su3_set_links", "su3_stage_links", "su3_stage_links_ex", "su3_apply_links", "su3_measurement_latest", "su3_measurement_latest_async", "su3_synchronize", "su3_stats", "su3_action", "su3_action_reset", "su3_set_sweep_counter", "su3_lattice_info", "su3_set_launch",
     "su3_autotune", "su3_use_graph", "su3_set_profiling", "su3_get_profile", "su3_ensemble_create", "su3_ensemble_destroy", "su3_ensemble_sweep",
     "su3_ensemble_measure", "su3_ensemble_get_links", "su3_ensemble_measurements", "su3_ensemble_set_launch", "su3_ensemble_autotune", "su3_ensemble_use_graph",
     "su3_ensemble_set_profiling", "su3_ensemble_get_profile",
@@ -109,6 +109,8 @@ def lib():
             "su3_stage_links": (c_int, [vp, dp, sz]),
             "su3_stage_links_ex": (c_int, [vp, c_void_p, sz, c_int]),
             "su3_measurement_latest": (c_int, [vp, dp, sz]),
+            "su3_measurement_latest_async": (c_int, [vp, dp, sz]),
+            "su3_synchronize": (c_int, [vp]),
             "su3_apply_links": (c_int, [vp]),
             "su3_stats": (c_int, [vp, u64p, u64p, u64p]),
             "su3_set_sweep_counter": (c_int, [vp, c_uint64]),
@@ -257,6 +259,16 @@ def su3_measurement_latest(h, nlayers: int) -> np.ndarray:
     out = np.zeros(5 * (nlayers + 1), dtype=np.float64)
     _check(lib().su3_measurement_latest(h, _dp(out), out.size))
     return out.reshape(nlayers + 1, 5)
+
+
+def su3_measurement_latest_async(h, out: np.ndarray):
+    """out: float64, C-contiguous, >= 5 * (nlayers + 1) values, ideally in
+    page-locked memory; valid after the stream reaches the copy."""
+    _check(lib().su3_measurement_latest_async(h, _dp(out), out.size))
+
+
+def su3_synchronize(h):
+    _check(lib().su3_synchronize(h))
 
 
 def su3_stats(h):
@@ -433,6 +445,15 @@ class Lattice:
         """The last measurement recorded by measure_every: [layer.., all] x
         (total, space, time, poly_re, poly_im)."""
         return su3_measurement_latest(self.h, self.nlayers)
+
+    def latest_measurement_async(self, out: np.ndarray):
+        """Queue the copy of the last recorded measurement into `out`
+        (5 * (nlayers + 1) float64, page-locked for an asynchronous copy);
+        read it after synchronize() or an event on the lattice's stream."""
+        su3_measurement_latest_async(self.h, out)
+
+    def synchronize(self):
+        su3_synchronize(self.h)
 
     def apply_links(self):
         su3_apply_links(self.h)

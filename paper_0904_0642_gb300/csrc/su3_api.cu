@@ -815,7 +815,9 @@ struct Engine {
       ch.state.target = ch.state.sweep + (uint32_t)n;
       ch.state.active = 1;
     }
-    TRY(upload_states());
+    // the device states equal the mirror in stream order: arm them there
+    // (an upload from the host would have to wait for the queued work)
+    CU(launch_arm(d_state, (int)chains.size(), (uint32_t)n, stream));
     const long long T = ticks_to_finish();
     TRY(profiling ? profiled_ticks(T) : run_ticks(T));
     mirror_ticks(T);
@@ -1128,6 +1130,24 @@ extern "C" su3_status su3_measurement_latest(su3_lattice *lat, double *host_out,
   CU(cudaMemcpyAsync(e.h_pinned, ch.results + slot * per, per * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
   CU(cudaStreamSynchronize(e.stream));
   std::memcpy(host_out, e.h_pinned, per * sizeof(double));
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_measurement_latest_async(su3_lattice *lat, double *host_out, size_t n) {
+  LAT_CHECK(lat);
+  Engine &e = lat->eng;
+  const Chain &ch = e.chains[0];
+  const size_t per = (size_t)(ch.desc.nlayers + 1) * kMeasVals;
+  if (!host_out || n < per) return fail(SU3_EINVAL, "host_out holds %zu doubles, %zu needed", n, per);
+  if (ch.state.n_meas == 0) return fail(SU3_ENOTFOUND, "no measurement recorded yet (measure_every)");
+  const size_t slot = (size_t)((ch.state.n_meas - 1) % (uint32_t)ch.desc.result_cap);
+  CU(cudaMemcpyAsync(host_out, ch.results + slot * per, per * sizeof(double), cudaMemcpyDeviceToHost, e.stream));
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_synchronize(su3_lattice *lat) {
+  LAT_CHECK(lat);
+  CU(cudaStreamSynchronize(lat->eng.stream));
   return SU3_OK;
 }
 

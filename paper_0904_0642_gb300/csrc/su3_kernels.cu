@@ -674,6 +674,24 @@ __global__ void k_action_sum(const double *slots, int n, double *out) {
   if (threadIdx.x == 0) *out = v;
 }
 
+// Arm every chain of an engine for n more sweeps, in stream order (the host
+// mirror does the same): no host buffer, so nothing to synchronise on.
+__global__ void k_arm(ChainState *state, int nchains, uint32_t n) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nchains; c += gridDim.x * blockDim.x) {
+    ChainState s = state[c];
+    s.target = s.sweep + n;
+    s.active = 1;
+    state[c] = s;
+  }
+}
+
+cudaError_t launch_arm(ChainState *state, int nchains, uint32_t n, cudaStream_t st) {
+  if (nchains <= 0) return cudaSuccess;
+  const int grid = (nchains + 255) / 256 < 1024 ? (nchains + 255) / 256 : 1024;
+  k_arm<<<grid, 256, 0, st>>>(state, nchains, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_action_sum(const double *slots, int n, double *out, cudaStream_t st) {
   k_action_sum<<<1, 32, 0, st>>>(slots, n, out);
   return cudaGetLastError();

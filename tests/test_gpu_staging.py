@@ -107,3 +107,38 @@ def test_latest_measurement():
     assert ei.value.status == su3.SU3_ENOTFOUND
     lat.sweep(10)  # 5 measurements in a ring of 3
     assert np.array_equal(lat.latest_measurement(), lat.measurements()[-1])
+
+
+def test_latest_measurement_async_pipeline():
+    """su3_measurement_latest_async copies, in stream order, the measurement
+    of the sweeps queued before it: a pipelined loop that reads step k's
+    result while step k+1 runs gets every step's result, equal to the ring
+    read afterwards; sweeps no longer wait for the queued work."""
+    import torch
+    stream = torch.cuda.Stream()
+    lat = su3.Lattice([6, 6, 6, 4], beta=5.9, seed=7, storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT,
+                      measure_every=5, measure_capacity=64, reunit_every=5, stream=stream)
+    out = np.zeros(4, dtype=np.float64)
+    with pytest.raises(su3.Su3Error) as ei:
+        lat.latest_measurement_async(np.zeros(10))
+    assert ei.value.status == su3.SU3_ENOTFOUND
+    with pytest.raises(su3.Su3Error):
+        lat.sweep(5)
+        lat.latest_measurement_async(out)  # too small for 5 * 2 values
+    lat.synchronize()
+    bufs = [torch.empty(10, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    evs = [torch.cuda.Event() for _ in range(2)]
+    got = []
+    for k in range(6):
+        lat.sweep(5)
+        lat.latest_measurement_async(bufs[k % 2])
+        evs[k % 2].record(stream)
+        if k >= 1:
+            evs[(k - 1) % 2].synchronize()
+            got.append(bufs[(k - 1) % 2].copy())
+    evs[1].synchronize()
+    got.append(bufs[1].copy())
+    ring = lat.measurements()  # one per 5 sweeps: the first from the sweep above, then six
+    assert ring.shape[0] == 7
+    for k in range(6):
+        assert np.array_equal(got[k].reshape(2, 5), ring[k + 1])
