@@ -453,7 +453,7 @@ def main():
     value = world * args.steps * SWEEPS_PER_STEP * links / (ms_max * 1e-3)
     meas = lat.measurements()
     plaq_last = float(meas[-1, 1, 0]) if len(meas) else float("nan")
-    launches = args.steps * (2 * len(DIMS) * SWEEPS_PER_STEP + 2)
+    launches = args.steps * (2 * len(DIMS) * SWEEPS_PER_STEP + 3)  # k_arm + 80 update + reunit + measure ticks
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
