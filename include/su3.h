@@ -259,6 +259,13 @@ su3_status su3_autotune(su3_lattice *lat, int *variant, int *threads, int *ctas_
  * (on = 0).  Results are identical either way. */
 su3_status su3_use_graph(su3_lattice *lat, int on);
 
+/* Launch each update tick as a programmatic dependent of the previous one
+ * (on by default): the next tick is scheduled while the previous one ends
+ * and waits at its first instruction for the previous tick's completion
+ * and memory, so results are identical either way.  Where the driver
+ * refuses such launches the library falls back to ordinary ones. */
+su3_status su3_use_pdl(su3_lattice *lat, int on);
+
 /* Kernel timing.  With profiling on, su3_sweep launches its ticks one by
  * one (no graph) with a CUDA event pair around each on the handle's stream,
  * and su3_get_profile sums the device time per stage kind: update phases,

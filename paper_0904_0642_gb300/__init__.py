@@ -36,7 +36,7 @@ EXPORTED = [
     "su3_config_init", "su3_link_bytes", "su3_lattice_create", "su3_lattice_create_ex", "su3_lattice_destroy",
     "su3_sweep", "su3_reunitarize", "su3_plaquette", "su3_polyakov", "su3_measure_async", "su3_measurements",
     "su3_get_links", "su3_set_links", "su3_stage_links", "su3_stage_links_ex", "su3_apply_links", "su3_measurement_latest", "su3_measurement_latest_async", "su3_synchronize", "su3_stats", "su3_action", "su3_action_reset", "su3_set_sweep_counter", "su3_lattice_info", "su3_set_launch",
-    "su3_autotune", "su3_use_graph", "su3_set_profiling", "su3_get_profile", "su3_ensemble_create", "su3_ensemble_destroy", "su3_ensemble_sweep",
+    "su3_autotune", "su3_use_graph", "su3_use_pdl", "su3_set_profiling", "su3_get_profile", "su3_ensemble_create", "su3_ensemble_destroy", "su3_ensemble_sweep",
     "su3_ensemble_measure", "su3_ensemble_get_links", "su3_ensemble_measurements", "su3_ensemble_set_launch", "su3_ensemble_autotune", "su3_ensemble_use_graph",
     "su3_ensemble_set_profiling", "su3_ensemble_get_profile",
     "su3_server_create", "su3_server_submit", "su3_server_poll", "su3_server_wait", "su3_server_load",
@@ -120,6 +120,7 @@ def lib():
             "su3_set_launch": (c_int, [vp, c_int, c_int, c_int]),
             "su3_autotune": (c_int, [vp, POINTER(c_int), POINTER(c_int), POINTER(c_int), dp]),
             "su3_use_graph": (c_int, [vp, c_int]),
+            "su3_use_pdl": (c_int, [vp, c_int]),
             "su3_set_profiling": (c_int, [vp, c_int]),
             "su3_get_profile": (c_int, [vp, POINTER(su3_profile), c_int]),
             "su3_ensemble_set_profiling": (c_int, [vp, c_int]),
@@ -312,6 +313,10 @@ def su3_use_graph(h, on: bool):
     _check(lib().su3_use_graph(h, int(bool(on))))
 
 
+def su3_use_pdl(h, on: bool):
+    _check(lib().su3_use_pdl(h, int(bool(on))))
+
+
 def su3_set_profiling(h, on: bool):
     _check(lib().su3_set_profiling(h, int(bool(on))))
 
@@ -483,6 +488,9 @@ class Lattice:
 
     def use_graph(self, on=True):
         su3_use_graph(self.h, on)
+
+    def use_pdl(self, on=True):
+        su3_use_pdl(self.h, on)
 
     def set_profiling(self, on=True):
         su3_set_profiling(self.h, on)

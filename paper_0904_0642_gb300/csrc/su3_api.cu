@@ -358,6 +358,9 @@ struct Engine {
   int variant = 0;  // register variant of the tick kernel (launch_tick)
   int total_tiles = 0;
   bool use_graph = true;
+  // ticks launched as programmatic dependents of the previous tick (the
+  // launch overlaps the previous tick's end); dropped if the driver refuses
+  bool pdl = true;
   cudaGraphExec_t graph = nullptr;
   int graph_ticks = 0;
   bool tiles_dirty = true;
@@ -707,7 +710,14 @@ struct Engine {
 
   // One tick, and for a divided chain the halo refresh of what it changed.
   su3_status one_tick(int grid) {
-    CU(launch_tick(storage, variant, weighted_any, sub_any, args(), grid, block, stream));
+    cudaError_t e = launch_tick(storage, variant, weighted_any, sub_any, args(), grid, block, stream, pdl);
+    if (e != cudaSuccess && pdl) {  // not offered here: plain launches from now on
+      cudaGetLastError();
+      pdl = false;
+      drop_graph();
+      e = launch_tick(storage, variant, weighted_any, sub_any, args(), grid, block, stream, false);
+    }
+    CU(e);
     if (sub_any) CU(halo_refresh(d_desc, d_state, 0));
     return SU3_OK;
   }
@@ -748,23 +758,31 @@ struct Engine {
     if (graph) return SU3_OK;
     int grid = 0;
     TRY(grid_size(&grid));
-    cudaGraph_t g = nullptr;
-    CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < kGraphTicks; ++i) {
-      cudaError_t e = launch_tick(storage, variant, weighted_any, sub_any, args(), grid, block, stream);
-      if (e == cudaSuccess && sub_any) e = halo_refresh(d_desc, d_state, 0);
-      if (e != cudaSuccess) {
-        cudaStreamEndCapture(stream, &g);
-        if (g) cudaGraphDestroy(g);
-        return fail(SU3_ECUDA, "launch during capture: %s", cudaGetErrorString(e));
-      }
+    cudaError_t e = capture_graph(grid);
+    if (e != cudaSuccess && pdl) {  // programmatic edges not capturable here: plain ones
+      cudaGetLastError();
+      pdl = false;
+      e = capture_graph(grid);
     }
-    CU(cudaStreamEndCapture(stream, &g));
-    cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(SU3_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(SU3_ECUDA, "graph capture of %d ticks: %s", kGraphTicks, cudaGetErrorString(e));
     graph_ticks = kGraphTicks;
     return SU3_OK;
+  }
+
+  cudaError_t capture_graph(int grid) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < kGraphTicks && e == cudaSuccess; ++i) {
+      e = launch_tick(storage, variant, weighted_any, sub_any, args(), grid, block, stream, pdl);
+      if (e == cudaSuccess && sub_any) e = halo_refresh(d_desc, d_state, 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) graph = nullptr;
+    return e;
   }
 
   // Launch n ticks: whole graphs, then single launches for the remainder.
@@ -1269,6 +1287,14 @@ extern "C" su3_status su3_use_graph(su3_lattice *lat, int on) {
   LAT_CHECK(lat);
   CU(cudaStreamSynchronize(lat->eng.stream));
   lat->eng.use_graph = on != 0;
+  lat->eng.drop_graph();
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_use_pdl(su3_lattice *lat, int on) {
+  LAT_CHECK(lat);
+  CU(cudaStreamSynchronize(lat->eng.stream));
+  lat->eng.pdl = on != 0;
   lat->eng.drop_graph();
   return SU3_OK;
 }

@@ -529,7 +529,14 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
   __shared__ ChainDesc sd;
   __shared__ ChainState ss;
   __shared__ double s_red[32 * kPartVals];
+  // Launched as a programmatic dependent (pdl), this tick may be scheduled
+  // before the previous kernel of the stream has finished: wait for its
+  // completion and memory before touching anything, then let the next tick
+  // be scheduled.  Both are no-ops for an ordinary launch.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int total = ea.hdr->total_tiles;
+  const int nchains = ea.hdr->nchains;
   int cur = -1;
   uint32_t np = 0, na = 0;  // FHKP counters of the current chain, flushed per warp
   bool wrote_partials = false;  // this thread wrote data that the last warp reads
@@ -586,8 +593,29 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
   }
   prev = __shfl_sync(0xffffffffu, prev, 0);
   if (prev != gridDim.x * (blockDim.x >> 5) - 1) return;
+  if (nchains == 1 && cur == 0) {
+    // One chain, whose state and descriptor this CTA holds: no global reads
+    // and, outside measurement ticks, no fence (the next launch orders the
+    // state write).
+    ChainState st = ss;
+    if (st.active) {
+      if (st.stage == kStageMeasure) {
+        __threadfence();  // acquire the partials of every tile
+        double *out = sd.results + (size_t)(st.n_meas % (uint32_t)sd.result_cap) * (sd.nlayers + 1) * kMeasVals;
+        finalize_measure(sd, sd.partials, out);
+        st.n_meas += 1;
+      }
+      advance_stage(StageParams{sd.D, sd.reunit_every, sd.measure_every}, st);
+    } else {
+      st.prev_stage = -1;  // nothing ran: no halo refresh
+    }
+    if (lane == 0) {
+      ea.state[0] = st;
+      ea.hdr->done_warps = 0;
+    }
+    return;
+  }
   __threadfence();
-  const int nchains = ea.hdr->nchains;
   // chains in a measurement stage: 32 states read at a time (one lane each),
   // then each such chain finished by the whole warp
   for (int base = 0; base < nchains; base += 32) {
@@ -994,10 +1022,26 @@ constexpr int kSubVariant = 3;
 
 int tick_variants(int storage) { return storage == 1 ? 5 : 1; }
 
+// pdl: launch as a programmatic dependent of the previous kernel in the
+// stream (the tick waits for that kernel's completion and memory at its
+// first instruction, so only the launch itself overlaps the previous tick).
 template <class S, int V, bool WT, bool SUB = false>
-static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_t st) {
-  k_tick<S, V, WT, SUB><<<grid, block, 0, st>>>(ea);
-  return cudaGetLastError();
+static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_t st, bool pdl) {
+  if (!pdl) {
+    k_tick<S, V, WT, SUB><<<grid, block, 0, st>>>(ea);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_tick<S, V, WT, SUB>, ea);
 }
 
 template <class S, int V, bool WT, bool SUB = false>
@@ -1035,8 +1079,8 @@ static cudaError_t tick_dispatch(int storage, int variant, bool sub, A... a) {
 
 template <class S, int V, bool WT, bool SUB>
 struct TickLaunch {
-  static cudaError_t run(const EngineArgs *ea, int grid, int block, cudaStream_t st) {
-    return tick_v<S, V, WT, SUB>(*ea, grid, block, st);
+  static cudaError_t run(const EngineArgs *ea, int grid, int block, cudaStream_t st, bool pdl) {
+    return tick_v<S, V, WT, SUB>(*ea, grid, block, st, pdl);
   }
 };
 
@@ -1046,12 +1090,12 @@ struct TickOccupancy {
 };
 
 cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, const EngineArgs &ea, int grid, int block,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool pdl) {
   if (sub) variant = storage == 0 ? 0 : kSubVariant;
   if (block > tick_max_threads(storage, variant)) return cudaErrorInvalidConfiguration;
   const EngineArgs *pa = &ea;
-  return weighted ? tick_dispatch<TickLaunch, true>(storage, variant, sub, pa, grid, block, st)
-                  : tick_dispatch<TickLaunch, false>(storage, variant, sub, pa, grid, block, st);
+  return weighted ? tick_dispatch<TickLaunch, true>(storage, variant, sub, pa, grid, block, st, pdl)
+                  : tick_dispatch<TickLaunch, false>(storage, variant, sub, pa, grid, block, st, pdl);
 }
 
 cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, int all, int boxes,

@@ -16,7 +16,7 @@ namespace su3g {
 int tick_variants(int storage);
 int tick_max_threads(int storage, int variant);
 cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, const EngineArgs &ea, int grid, int block,
-                        cudaStream_t st);
+                        cudaStream_t st, bool pdl = false);
 // Halo refresh of a divided chain (after its tick, or all links), and the
 // copies between its sublattice boxes and the undivided layout.
 // boxes: layers x sublattices; halo_sites: halo sites of one box (both colours).

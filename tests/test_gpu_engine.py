@@ -67,11 +67,13 @@ def test_graph_and_launch_shape_do_not_change_links(storage):
     if storage == su3.SU3_FP32_12:
         shapes += [(1, 128, 0), (1, 96, 3), (2, 64, 0), (2, 128, 1), (3, 256, 2), (4, 256, 0), (4, 128, 3)]
     for variant, threads, ctas in shapes:
-        lat = su3.Lattice(dims, **kw)
-        lat.set_launch(threads, ctas, variant=variant)
-        lat.sweep(7)
-        assert np.array_equal(lat.get_links(), want), (variant, threads, ctas)
-        assert lat.stats() == ref.stats()
+        for pdl in (True, False):
+            lat = su3.Lattice(dims, **kw)
+            lat.set_launch(threads, ctas, variant=variant)
+            lat.use_pdl(pdl)
+            lat.sweep(7)
+            assert np.array_equal(lat.get_links(), want), (variant, threads, ctas, pdl)
+            assert lat.stats() == ref.stats()
 
 
 def test_resume_is_bitwise():
