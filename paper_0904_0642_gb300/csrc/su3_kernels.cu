@@ -615,39 +615,19 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
     }
     return;
   }
-  __threadfence();
-  // chains in a measurement stage: 32 states read at a time (one lane each),
-  // then each such chain finished by the whole warp
-  for (int base = 0; base < nchains; base += 32) {
-    const int c = base + lane;
-    bool meas = false;
-    uint32_t nm = 0;
-    if (c < nchains) {
-      const ChainState st = ea.state[c];
-      meas = st.active && st.stage == kStageMeasure;
-      nm = st.n_meas;
-    }
-    unsigned todo = __ballot_sync(0xffffffffu, meas);
-    while (todo) {
-      const int k = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const uint32_t n_meas = __shfl_sync(0xffffffffu, nm, k);
-      const ChainDesc &d = ea.desc[base + k];
-      double *out = d.results + (size_t)(n_meas % (uint32_t)d.result_cap) * (d.nlayers + 1) * kMeasVals;
-      finalize_measure(d, d.partials, out);
-    }
-  }
-  __syncwarp();
-  __threadfence();
-  // advance every chain's stage machine: four chains per lane in flight, so
-  // that their loads overlap
+  // Every chain's state is read once (four per lane in flight, so that
+  // their loads overlap; the previous launch ordered them), chains in a
+  // measurement stage are finished by the whole warp, then every state is
+  // advanced and written.  A fence (acquiring the tiles' partials) only
+  // when some chain measures.
   constexpr int kU = 4;
-  for (int base = lane; base < nchains; base += 32 * kU) {
+  bool fenced = false;
+  for (int base = 0; base < nchains; base += 32 * kU) {
     ChainState st[kU];
     StageParams sp[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
-      const int c = base + 32 * u;
+      const int c = base + 32 * u + lane;
       if (c < nchains) {
         st[u] = ea.state[c];
         const ChainDesc &d = ea.desc[c];
@@ -656,7 +636,25 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
-      const int c = base + 32 * u;
+      const int c = base + 32 * u + lane;
+      const bool meas = c < nchains && st[u].active && st[u].stage == kStageMeasure;
+      unsigned todo = __ballot_sync(0xffffffffu, meas);
+      if (todo && !fenced) {
+        __threadfence();
+        fenced = true;
+      }
+      while (todo) {
+        const int k = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t n_meas = __shfl_sync(0xffffffffu, st[u].n_meas, k);
+        const ChainDesc &d = ea.desc[base + 32 * u + k];
+        double *out = d.results + (size_t)(n_meas % (uint32_t)d.result_cap) * (d.nlayers + 1) * kMeasVals;
+        finalize_measure(d, d.partials, out);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int c = base + 32 * u + lane;
       if (c >= nchains) continue;
       if (!st[u].active) {
         if (st[u].prev_stage != -1) ea.state[c].prev_stage = -1;  // nothing ran: no halo refresh
