@@ -352,9 +352,12 @@ __device__ __forceinline__ void measure_site(const ChainDesc &d, int layer, int 
     for (int mu = 0; mu + 1 < D; ++mu) {
       const int xmu = sel(g.x, mu);
       const M3<R> um = S::load(plane_ptr<S>(d, layer, colour, mu), Vh, g.s >> 1);  // U_mu(x)
-#pragma unroll 1
-      for (int nu = mu + 1; nu < D; ++nu) {
-        const double p = plaquette_at<S, SUB>(d, g, colour, mu, nu, xmu, sel(g.x, nu), um);
+      // unrolled over a fixed bound so that the loads of the plaquettes
+      // of this mu can be in flight together
+#pragma unroll
+      for (int nu = 1; nu < kMaxD; ++nu) {
+        if (nu <= mu || nu >= D) continue;
+        const double p = plaquette_at<S, SUB>(d, g, colour, mu, nu, xmu, g.x[nu], um);
         if (nu == D - 1) acc[1] += p; else acc[0] += p;
       }
     }
