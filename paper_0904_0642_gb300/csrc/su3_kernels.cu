@@ -673,10 +673,20 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
 
 // ------------------------------------------------------------------ stand-alone measurement
 
+// The CTA's shared copy of a chain descriptor (a per-thread copy of the
+// struct would live in local memory).
+__device__ __forceinline__ void desc_to_shared(ChainDesc &dst, const ChainDesc *src) {
+  const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+  uint32_t *d = reinterpret_cast<uint32_t *>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(ChainDesc) / 4); i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+}
+
 template <class S>
 __global__ void __launch_bounds__(256) k_measure(ChainDesc *desc_dev) {
   __shared__ double s_red[32 * kPartVals];
-  const ChainDesc d = *desc_dev;
+  __shared__ ChainDesc d;
+  desc_to_shared(d, desc_dev);
   const int total = d.tiles_per_layer * d.nlayers;
   for (int lt = blockIdx.x; lt < total; lt += gridDim.x) {
     const int layer = lt / d.tiles_per_layer;
@@ -730,7 +740,8 @@ cudaError_t launch_action_sum(const double *slots, int n, double *out, cudaStrea
 
 template <class S>
 __global__ void k_start(ChainDesc *desc_dev, int hot) {
-  const ChainDesc d = *desc_dev;
+  __shared__ ChainDesc d;
+  desc_to_shared(d, desc_dev);
   const size_t nl = (size_t)d.nlayers * 2 * d.D * d.Vh;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nl; i += (size_t)gridDim.x * blockDim.x) {
     const int jj = (int)(i % d.Vh);
@@ -776,7 +787,8 @@ __global__ void k_start(ChainDesc *desc_dev, int hot) {
 
 template <class S>
 __global__ void k_convert(ChainDesc *desc_dev, double *canon, int to_canonical) {
-  const ChainDesc d = *desc_dev;
+  __shared__ ChainDesc d;
+  desc_to_shared(d, desc_dev);
   const size_t nlinks = (size_t)d.nlayers * d.V * d.D;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nlinks; i += (size_t)gridDim.x * blockDim.x) {
     const int mu = (int)(i % d.D);
@@ -910,7 +922,8 @@ __global__ void k_sub_copy(const ChainDesc *sub_dev, const ChainDesc *plain_dev,
 // [layer][i_s - 1][mu][row][col][re, im]); row 3 = conj(row1 x row2).
 template <class S>
 __global__ void k_convert_rows2(ChainDesc *desc_dev, const float *src) {
-  const ChainDesc d = *desc_dev;
+  __shared__ ChainDesc d;
+  desc_to_shared(d, desc_dev);
   const size_t nlinks = (size_t)d.nlayers * d.V * d.D;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nlinks; i += (size_t)gridDim.x * blockDim.x) {
     const int mu = (int)(i % d.D);
