@@ -335,8 +335,8 @@ __device__ __forceinline__ void acc_su3_2rows_w(M3<R> &A, const M3<R> &m, R w) {
 //
 // Links of one chain: Vec planes [layer][colour][mu][q][jj], jj the
 // checkerboard index (i_s - 1) / 2 of the site within its layer, so a warp
-// of consecutive sites reads each q-vector as one contiguous 512-byte line
-// of 128-bit loads.
+// of consecutive sites reads each q-vector as one contiguous line (512
+// bytes of 128-bit loads; the float2 plane of the 18-real float form 256).
 
 // Every form has load (3 rows), load2 (rows 1, 2; row 3 left unset), store
 // and copy (one link between two planes, for halo and box copies).
