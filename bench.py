@@ -184,15 +184,30 @@ def run_reference(args):
 
 
 def cpu_baseline():
-    """One full oracle sweep of the 32^4 hot-start lattice on one core."""
+    """One full oracle sweep of the 32^4 hot-start lattice on one core, and
+    the same sweep with the oracle's OpenMP loop over the sites of a phase
+    on every host core (identical links)."""
     import oracle
     lat = oracle.Lattice(DIMS).hot_start(SEED)
     t0 = time.perf_counter()
     lat.sweep(BETA, HITS, SEED, n=1)
     dt = time.perf_counter() - t0
-    return {"value": lat.nlinks / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one full sweep (4194304 link updates) of the 32^4 hot-start lattice, single thread, FP64",
-            "seconds": dt}
+    out = {"value": lat.nlinks / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "one full sweep (4194304 link updates) of the 32^4 hot-start lattice, single thread, FP64",
+           "seconds": dt}
+    ncores = oracle.available_threads()
+    if ncores > 1:
+        lat = oracle.Lattice(DIMS).hot_start(SEED)
+        oracle.set_threads(ncores)
+        try:
+            t0 = time.perf_counter()
+            lat.sweep(BETA, HITS, SEED, n=1)
+            dt = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(1)
+        out["all_cores"] = {"value": lat.nlinks / dt, "unit": UNIT, "cores": ncores, "seconds": dt,
+                            "sample": "the same sweep, OpenMP over the sites of each phase"}
+    return out
 
 
 # ---------------------------------------------------------------- other workloads

@@ -41,6 +41,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXD 8
 #define ORC_TWO_PI 6.283185307179586476925286766559
@@ -589,6 +592,23 @@ void orc_link_chain(double *u18, const double *A18, double beta, int hits, uint6
 /* order, initialised by the caller).                                     */
 /* ------------------------------------------------------------------ */
 
+/* Threads for the sites of one phase (1 unless set).  The links updated in
+ * one phase are independent -- each staple reads only links of the other
+ * colour or of other directions (Sec. 2) -- and every random number is a
+ * function of its counter, so any number of threads gives the same links
+ * bit for bit. */
+static int orc_threads = 1;
+
+void orc_set_threads(int n) { orc_threads = n < 1 ? 1 : n; }
+
+int orc_available_threads(void) {
+#ifdef _OPENMP
+  return omp_get_num_procs();
+#else
+  return 1;
+#endif
+}
+
 /* One (colour, direction) phase over the sites s_begin <= i_s - 1 < s_end
  * of every layer (the whole phase for [0, V)). */
 void orc_phase(const orc_geom *g, double *U, double beta, double beta1, int hits, uint64_t seed, int64_t sweep,
@@ -596,7 +616,11 @@ void orc_phase(const orc_geom *g, double *U, double beta, double beta1, int hits
   int64_t V = orc_nsites(g);
   if (s_end > V) s_end = V;
   const int weighted = g->nlayers == 2 && beta1 != beta; /* Sec. 2.2, two couplings */
-  for (int l = 0; l < g->nlayers; ++l)
+  for (int l = 0; l < g->nlayers; ++l) {
+    uint64_t nprop = 0, nacc = 0;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(orc_threads) schedule(static) reduction(+ : nprop, nacc) if (orc_threads > 1)
+#endif
     for (int64_t s = s_begin; s < s_end; ++s) {
       int32_t x[ORC_MAXD];
       orc_site_coords(g, s, x);
@@ -609,11 +633,14 @@ void orc_phase(const orc_geom *g, double *U, double beta, double beta1, int hits
       orc_cm_update(&Ul, &A, weighted ? 1.0 : beta, hits, seed, orc_site_key(g, l, s), (uint32_t)sweep, colour, mu,
                     &st);
       m_store(p, &Ul);
-      if (stats) { stats[0] += st.proposals; stats[1] += st.accepts; }
+      nprop += st.proposals;
+      nacc += st.accepts;
       int64_t idx = ((int64_t)l * V + s) * g->D + mu;
       if (margins && st.margin < margins[idx]) margins[idx] = st.margin;
       if (kmins && st.kmin < kmins[idx]) kmins[idx] = st.kmin;
     }
+    if (stats) { stats[0] += nprop; stats[1] += nacc; }
+  }
 }
 
 void orc_sweep(const orc_geom *g, double *U, double beta, double beta1, int hits, uint64_t seed, int64_t sweep0,

@@ -134,3 +134,23 @@ def test_acceptance_in_scaling_region():
     lat.sweep(6.0, 1, 3, n=30)
     prop, acc = lat.sweep(6.0, 1, 3, n=20)
     assert 0.95 < acc / prop < 0.995
+
+
+def test_threads_give_identical_sweeps():
+    """OpenMP over the sites of a phase (the SURVEY's all-cores oracle
+    timing): the links of one phase are independent and every random number
+    is a function of its counter, so threads change nothing, bit for bit."""
+    dims = [4, 4, 2, 4]
+    a = oracle.Lattice(dims).hot_start(3)
+    b = oracle.Lattice(dims).hot_start(3)
+    ma = np.full(a.nlinks, np.inf)
+    mb = np.full(b.nlinks, np.inf)
+    try:
+        oracle.set_threads(1)
+        sa = a.sweep(5.7, 3, 11, n=2, margins=ma)
+        oracle.set_threads(4)
+        sb = b.sweep(5.7, 3, 11, n=2, margins=mb)
+    finally:
+        oracle.set_threads(1)
+    assert sa == sb
+    assert np.array_equal(a.U, b.U) and np.array_equal(ma, mb)
