@@ -12,6 +12,8 @@
 * The paper's own numbers: 4^4, beta = 5.6, ordered start (Sec. 3.1.1).
 """
 import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -137,20 +139,21 @@ def test_acceptance_in_scaling_region():
 
 
 def test_threads_give_identical_sweeps():
-    """OpenMP over the sites of a phase (the SURVEY's all-cores oracle
-    timing): the links of one phase are independent and every random number
-    is a function of its counter, so threads change nothing, bit for bit."""
-    dims = [4, 4, 2, 4]
-    a = oracle.Lattice(dims).hot_start(3)
-    b = oracle.Lattice(dims).hot_start(3)
-    ma = np.full(a.nlinks, np.inf)
-    mb = np.full(b.nlinks, np.inf)
-    try:
-        oracle.set_threads(1)
-        sa = a.sweep(5.7, 3, 11, n=2, margins=ma)
-        oracle.set_threads(4)
-        sb = b.sweep(5.7, 3, 11, n=2, margins=mb)
-    finally:
-        oracle.set_threads(1)
-    assert sa == sb
-    assert np.array_equal(a.U, b.U) and np.array_equal(ma, mb)
+    """OpenMP over the sites of a phase (the all-cores oracle timing): the
+    links of one phase are independent and every random number is a
+    function of its counter, so threads change nothing, bit for bit.  Run in
+    a fresh interpreter, so that this process never starts OpenMP threads
+    (later tests fork)."""
+    code = (
+        "import numpy as np, oracle\n"
+        "dims = [4, 4, 2, 4]\n"
+        "a = oracle.Lattice(dims).hot_start(3); b = oracle.Lattice(dims).hot_start(3)\n"
+        "ma = np.full(a.nlinks, np.inf); mb = np.full(b.nlinks, np.inf)\n"
+        "oracle.set_threads(1); sa = a.sweep(5.7, 3, 11, n=2, margins=ma)\n"
+        "oracle.set_threads(4); sb = b.sweep(5.7, 3, 11, n=2, margins=mb)\n"
+        "assert sa == sb, (sa, sb)\n"
+        "assert np.array_equal(a.U, b.U) and np.array_equal(ma, mb)\n"
+        "print('identical')\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "identical" in r.stdout, r.stderr
