@@ -199,7 +199,10 @@ su3_status su3_set_links(su3_lattice *lat, const double *host, size_t n);
  * su3_apply_links makes the lattice's stream wait for that copy, then
  * converts the staged links into the lattice (divided lattices: scatter and
  * halo refresh) and restarts the action bookkeeping, all queued on the
- * stream without blocking the host; EINVAL when nothing is staged.  The
+ * stream without blocking the host; EINVAL when nothing is staged.  With
+ * measure_every > 0 (one coupling) the bookkeeping restarts at the next
+ * recorded measurement, which measures the action anyway, instead of with a
+ * measurement of its own (su3_action before then restarts it on the spot).  The
  * host buffer is read asynchronously: keep it unchanged until a
  * synchronising call on the lattice (su3_plaquette, su3_get_links, ...)
  * has returned after the matching su3_apply_links. */
@@ -226,7 +229,8 @@ su3_status su3_stats(su3_lattice *lat, uint64_t *proposals, uint64_t *accepts, u
  * last reset + the booked changes since (summed in a fixed order); *direct =
  * the action recomputed from the plaquette now (NaN for the two-coupling DLT;
  * its *booked is then the change since the last reset).  Re-unitarisation
- * and su3_set_links are not booked; su3_set_links resets.  Synchronises.
+ * and su3_set_links are not booked; su3_set_links resets (su3_apply_links
+ * too, possibly at the next recorded measurement).  Synchronises.
  * su3_action_reset sets the reference to the direct action and clears the
  * booked changes. */
 su3_status su3_action(su3_lattice *lat, double *booked, double *direct);

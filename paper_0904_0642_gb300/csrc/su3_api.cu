@@ -239,6 +239,8 @@ static void fill_desc(Chain &ch, int tile) {
   ChainDesc &d = ch.desc;
   d.links = ch.links;
   d.action_slots = ch.action_slots;
+  d.ref_meas = ch.ref_meas;
+  d.n_action_slots = ch.n_action_slots;
   d.halo = ch.d_halo;
   d.halo_n[0] = ch.halo_n[0];
   d.halo_n[1] = ch.halo_n[1];
@@ -807,7 +809,10 @@ struct Engine {
       ChainState s = ch.state;
       long long t = 0;
       while (s.active) {
-        if (s.stage == kStageMeasure) s.n_meas += 1;
+        if (s.stage == kStageMeasure) {
+          s.n_meas += 1;
+          s.anchor = 0;
+        }
         host_advance_stage(ch.desc, s);
         ++t;
       }
@@ -820,7 +825,10 @@ struct Engine {
   void mirror_ticks(long long n) {
     for (auto &ch : chains)
       for (long long t = 0; t < n && ch.state.active; ++t) {
-        if (ch.state.stage == kStageMeasure) ch.state.n_meas += 1;
+        if (ch.state.stage == kStageMeasure) {
+          ch.state.n_meas += 1;
+          ch.state.anchor = 0;  // the device restarted the bookkeeping there
+        }
         host_advance_stage(ch.desc, ch.state);
       }
   }
@@ -918,6 +926,10 @@ struct Engine {
   // order and without waiting (su3_action reads the reference).
   su3_status action_reset(size_t c) {
     Chain &ch = chains[c];
+    if (ch.state.anchor) {  // restarting now: no restart at the next measurement
+      CU(launch_set_anchor(d_state + c, 0, stream));
+      ch.state.anchor = 0;
+    }
     CU(cudaMemsetAsync(ch.action_slots, 0, (size_t)ch.n_action_slots * sizeof(double), stream));
     if (!ch.desc.weighted) {
       ChainDesc *dd = nullptr;
@@ -925,6 +937,18 @@ struct Engine {
       const ChainDesc &md = ch.sub ? ch.pdesc : ch.desc;
       CU(launch_measure(storage, dd, md.nlayers * md.tiles_per_layer, block, ch.ref_meas, stream));
     }
+    return SU3_OK;
+  }
+
+  // Links replaced without bookkeeping, for a chain that records
+  // measurements: the bookkeeping restarts at its next recorded measurement
+  // (which measures the action anyway), not with a measurement of its own;
+  // su3_action before that restarts it on the spot.  Otherwise at once.
+  su3_status action_defer(size_t c) {
+    Chain &ch = chains[c];
+    if (ch.desc.weighted || ch.desc.measure_every <= 0) return action_reset(c);
+    CU(launch_set_anchor(d_state + c, 1, stream));
+    ch.state.anchor = 1;
     return SU3_OK;
   }
 
@@ -1231,7 +1255,7 @@ extern "C" su3_status su3_apply_links(su3_lattice *lat) {
   CU(cudaEventRecord(lat->consumed[b], e.stream));
   lat->used[b] = true;
   lat->pending = -1;
-  return e.action_reset(0);  // the links changed without bookkeeping
+  return e.action_defer(0);  // the links changed without bookkeeping
 }
 
 extern "C" su3_status su3_stats(su3_lattice *lat, uint64_t *proposals, uint64_t *accepts, uint64_t *sweeps) {
@@ -1245,6 +1269,8 @@ extern "C" su3_status su3_action(su3_lattice *lat, double *booked, double *direc
   LAT_CHECK(lat);
   Engine &e = lat->eng;
   if (e.tiles_dirty) TRY(e.rebuild());
+  // a restart still waiting for the next measurement happens now
+  if (e.chains[0].state.anchor) TRY(e.action_reset(0));
   double dS = 0.0, S = 0.0, ref = 0.0;
   TRY(e.booked_change(0, &dS));
   TRY(e.action_reference(0, &ref));

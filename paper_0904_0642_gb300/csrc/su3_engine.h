@@ -45,6 +45,8 @@ struct ChainDesc {
   double *partials;          // [tiles][kPartVals]
   unsigned long long *counters;  // [proposals, accepts]
   double *action_slots;      // booked action changes, one slot per warp of sites: [layer][ceil(Vh/32)]
+  double *ref_meas;          // the measurement the booked changes count from: [nlayers + 1][kMeasVals]
+  int32_t n_action_slots;
   uint32_t seed_lo, seed_hi;
   int32_t D, nlayers, glue_mask, layer_blind;
   int32_t custom_period;     // 0: site key = layer*V + i_s - 1
@@ -98,7 +100,8 @@ struct ChainState {
   int32_t active;          // 1: advancing; 0: idle
   uint32_t n_meas;         // measurements recorded
   int32_t prev_stage;      // stage run by the last tick (-1: none); read by the halo refresh
-  int32_t pad[2];
+  int32_t anchor;          // 1: the next measurement restarts the action bookkeeping
+  int32_t pad;
 };
 
 struct EngineHeader {

@@ -449,6 +449,17 @@ __device__ void finalize_measure(const ChainDesc &d, const double *partials, dou
   }
 }
 
+// The action bookkeeping restarts at this measurement (a chain whose links
+// were replaced asks for it): the measurement becomes the reference and
+// the booked changes restart from zero.  Warp-collective; the measurement
+// was written by lane 0 of this warp.
+__device__ __forceinline__ void restart_bookkeeping(const ChainDesc &d, const double *out) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < (d.nlayers + 1) * kMeasVals; i += 32) d.ref_meas[i] = out[i];
+  for (int i = lane; i < d.n_action_slots; i += 32) d.action_slots[i] = 0.0;
+}
+
 // ------------------------------------------------------------------ tick kernel
 
 __device__ __forceinline__ void load_chain(const EngineArgs &ea, int c, ChainDesc &sd, ChainState &ss) {
@@ -606,6 +617,10 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
         __threadfence();  // acquire the partials of every tile
         double *out = sd.results + (size_t)(st.n_meas % (uint32_t)sd.result_cap) * (sd.nlayers + 1) * kMeasVals;
         finalize_measure(sd, sd.partials, out);
+        if (st.anchor) {
+          restart_bookkeeping(sd, out);
+          st.anchor = 0;
+        }
         st.n_meas += 1;
       }
       advance_stage(StageParams{sd.D, sd.reunit_every, sd.measure_every}, st);
@@ -650,10 +665,13 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
         const int k = __ffs(todo) - 1;
         todo &= todo - 1;
         const uint32_t n_meas = __shfl_sync(0xffffffffu, st[u].n_meas, k);
+        const int anchor = __shfl_sync(0xffffffffu, st[u].anchor, k);
         const ChainDesc &d = ea.desc[base + 32 * u + k];
         double *out = d.results + (size_t)(n_meas % (uint32_t)d.result_cap) * (d.nlayers + 1) * kMeasVals;
         finalize_measure(d, d.partials, out);
+        if (anchor) restart_bookkeeping(d, out);
       }
+      if (meas) st[u].anchor = 0;
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
@@ -722,6 +740,14 @@ __global__ void k_arm(ChainState *state, int nchains, uint32_t n) {
     s.active = 1;
     state[c] = s;
   }
+}
+
+// Set the bookkeeping-restart flag of one chain, in stream order.
+__global__ void k_set_anchor(ChainState *state, int value) { state->anchor = value; }
+
+cudaError_t launch_set_anchor(ChainState *state, int value, cudaStream_t st) {
+  k_set_anchor<<<1, 1, 0, st>>>(state, value);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_arm(ChainState *state, int nchains, uint32_t n, cudaStream_t st) {

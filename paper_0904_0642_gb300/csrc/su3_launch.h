@@ -35,6 +35,7 @@ void host_advance_stage(const ChainDesc &d, ChainState &s);
 // Fixed-order sum of n booked action-change slots into *out (device).
 cudaError_t launch_action_sum(const double *slots, int n, double *out, cudaStream_t st);
 cudaError_t launch_arm(ChainState *state, int nchains, uint32_t n, cudaStream_t st);
+cudaError_t launch_set_anchor(ChainState *state, int value, cudaStream_t st);
 // Measurement with partial sums in the library's static device scratch
 // (su3_measure_noalloc); the descriptor is passed by value.
 int noalloc_max_tiles();

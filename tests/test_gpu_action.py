@@ -89,3 +89,33 @@ def test_two_couplings_booked_change_matches_oracle_weighted_action():
     o.U[...] = lat.get_links()
     s_after = sum_beta - o.action_weighted(6.0, 4.5)
     assert booked == pytest.approx(s_after - s_before, rel=1e-10)
+
+
+@pytest.mark.parametrize("storage,rel", [(su3.SU3_FP64_18, 1e-11), (su3.SU3_FP32_12, 2e-6)])
+def test_apply_links_restarts_bookkeeping_at_next_measurement(storage, rel):
+    """A lattice that records measurements restarts the bookkeeping after
+    su3_apply_links at its next measurement (which measures the action
+    anyway): the booked action then follows the direct one from there.
+    Asked before any measurement, su3_action restarts it on the spot."""
+    dims = [6, 6, 6, 6]
+    lat = su3.Lattice(dims, beta=6.0, seed=3, storage=storage, start=su3.SU3_START_HOT, measure_every=5,
+                      reunit_every=5)
+    start = oracle.Lattice(dims).hot_start(77).U
+    lat.sweep(7)
+    lat.stage_links(start)
+    lat.apply_links()
+    lat.sweep(8)  # the restart is the measurement after sweep 5 of these
+    meas = lat.measurements()[-2]  # that measurement (the last one is after sweep 10)
+    b, d = lat.action()
+    assert b == pytest.approx(d, rel=rel)
+    # the reference was that measurement: booked - (changes since) is its action
+    np_ = 6 ** 4 * 6
+    assert meas.shape == (2, 5)
+    lat.stage_links(start)
+    lat.apply_links()
+    b, d = lat.action()  # no measurement since: restarted now
+    assert b == d
+    assert d == pytest.approx(6.0 * np_ * (1 - oracle.Lattice(dims).hot_start(77).plaquette()[0]), rel=1e-6)
+    lat.sweep(3)
+    b, d = lat.action()
+    assert b == pytest.approx(d, rel=rel)
