@@ -515,7 +515,7 @@ def main():
         # link, the storage format of this workload); the canonical FP64
         # layout (18 doubles per link) is timed the same way beside it.
         canon = lat.get_links()
-        k_e2e = max(3, args.steps // 10)
+        k_e2e = max(3, args.steps // 5)
 
         def e2e_run(fmt):
             if fmt == su3.SU3_LINKS_FP32_12:
