@@ -92,22 +92,23 @@ def test_resume_is_bitwise():
     assert np.array_equal(a.get_links(), c.get_links())
 
 
-def _mixed_configs():
+def _mixed_configs(storage=su3.SU3_FP32_12):
     rng = np.random.default_rng(42)
     shapes = [[8, 8, 8, 8], [6, 4, 8, 4], [8, 8, 8], [4, 4, 4, 4], [12, 12, 12]]
     cfgs = []
     for i, dims in enumerate(shapes * 2):
         boundary = su3.SU3_DLT if i in (3, 7) else su3.SU3_PBC
         cfgs.append(su3.make_config(dims, boundary=boundary, beta=float(rng.uniform(5.5, 6.5)), seed=1000 + i,
-                                    storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT, hits=1 + i % 3,
+                                    storage=storage, start=su3.SU3_START_HOT, hits=1 + i % 3,
                                     reunit_every=4))
     return cfgs
 
 
-def test_chain_alone_equals_chain_in_mixed_ensemble():
+@pytest.mark.parametrize("storage", [su3.SU3_FP32_12, su3.SU3_FP32_18, su3.SU3_FP64_18])
+def test_chain_alone_equals_chain_in_mixed_ensemble(storage):
     """Chains of different D, shape, boundary, beta, seed and hits advanced
     in one fused launch per tick give the same links as each chain alone."""
-    cfgs = _mixed_configs()
+    cfgs = _mixed_configs(storage)
     ens = su3.Ensemble(cfgs)
     ens.sweep(6)
     meas = ens.measure()
