@@ -91,15 +91,17 @@ def test_two_couplings_booked_change_matches_oracle_weighted_action():
     assert booked == pytest.approx(s_after - s_before, rel=1e-10)
 
 
-@pytest.mark.parametrize("storage,rel", [(su3.SU3_FP64_18, 1e-11), (su3.SU3_FP32_12, 2e-6)])
-def test_apply_links_restarts_bookkeeping_at_next_measurement(storage, rel):
+@pytest.mark.parametrize("storage,rel,ndiv", [(su3.SU3_FP64_18, 1e-11, None), (su3.SU3_FP32_12, 2e-6, None),
+                                              (su3.SU3_FP64_18, 1e-11, [2, 1, 1, 2])])
+def test_apply_links_restarts_bookkeeping_at_next_measurement(storage, rel, ndiv):
     """A lattice that records measurements restarts the bookkeeping after
     su3_apply_links at its next measurement (which measures the action
     anyway): the booked action then follows the direct one from there.
-    Asked before any measurement, su3_action restarts it on the spot."""
-    dims = [6, 6, 6, 6]
+    Asked before any measurement, su3_action restarts it on the spot.  Also
+    for a lattice divided into sublattice boxes (measured in the boxes)."""
+    dims = [4, 6, 6, 4] if ndiv else [6, 6, 6, 6]
     lat = su3.Lattice(dims, beta=6.0, seed=3, storage=storage, start=su3.SU3_START_HOT, measure_every=5,
-                      reunit_every=5)
+                      reunit_every=5, ndiv=ndiv)
     start = oracle.Lattice(dims).hot_start(77).U
     lat.sweep(7)
     lat.stage_links(start)
@@ -108,8 +110,7 @@ def test_apply_links_restarts_bookkeeping_at_next_measurement(storage, rel):
     meas = lat.measurements()[-2]  # that measurement (the last one is after sweep 10)
     b, d = lat.action()
     assert b == pytest.approx(d, rel=rel)
-    # the reference was that measurement: booked - (changes since) is its action
-    np_ = 6 ** 4 * 6
+    np_ = int(np.prod(dims)) * 6
     assert meas.shape == (2, 5)
     lat.stage_links(start)
     lat.apply_links()
