@@ -1341,10 +1341,16 @@ extern "C" su3_status su3_get_profile(su3_lattice *lat, su3_profile *out, int re
 static su3_status autotune_engine(Engine &e, int *variant, int *threads, int *ctas, double *us) {
   if (e.tiles_dirty) TRY(e.rebuild());
   CU(cudaStreamSynchronize(e.stream));
-  std::vector<void *> backup(e.chains.size(), nullptr);
+  // links and booked action changes are restored after the timing sweeps
+  std::vector<void *> backup(e.chains.size(), nullptr), slots(e.chains.size(), nullptr);
   for (size_t c = 0; c < e.chains.size(); ++c) {
+    const size_t sb = (size_t)e.chains[c].n_action_slots * sizeof(double);
     CU(cudaMalloc(&backup[c], e.chains[c].link_bytes));
     CU(cudaMemcpyAsync(backup[c], e.chains[c].links, e.chains[c].link_bytes, cudaMemcpyDeviceToDevice, e.stream));
+    if (sb) {
+      CU(cudaMalloc(&slots[c], sb));
+      CU(cudaMemcpyAsync(slots[c], e.chains[c].action_slots, sb, cudaMemcpyDeviceToDevice, e.stream));
+    }
   }
   std::vector<ChainState> saved_state;
   std::vector<unsigned long long> saved_cnt(2 * e.chains.size());
@@ -1404,11 +1410,15 @@ static su3_status autotune_engine(Engine &e, int *variant, int *threads, int *ct
   for (size_t c = 0; c < e.chains.size(); ++c) {
     e.chains[c].cfg.measure_every = saved_meas[c];
     cudaMemcpyAsync(e.chains[c].links, backup[c], e.chains[c].link_bytes, cudaMemcpyDeviceToDevice, e.stream);
+    if (slots[c])
+      cudaMemcpyAsync(e.chains[c].action_slots, slots[c], (size_t)e.chains[c].n_action_slots * sizeof(double),
+                      cudaMemcpyDeviceToDevice, e.stream);
     cudaMemcpyAsync(e.chains[c].counters, &saved_cnt[2 * c], 16, cudaMemcpyHostToDevice, e.stream);
     e.chains[c].state = saved_state[c];
   }
   cudaStreamSynchronize(e.stream);
   for (void *p : backup) cudaFree(p);
+  for (void *p : slots) cudaFree(p);
   e.profiling = saved_prof;
   if (st != SU3_OK) return st;
   e.use_graph = saved_graph;

@@ -120,3 +120,18 @@ def test_apply_links_restarts_bookkeeping_at_next_measurement(storage, rel, ndiv
     lat.sweep(3)
     b, d = lat.action()
     assert b == pytest.approx(d, rel=rel)
+
+
+def test_autotune_leaves_the_bookkeeping_alone():
+    """The autotuner's timing sweeps run on saved links and restore them
+    afterwards, together with the booked changes: the booked action still
+    follows the direct one."""
+    lat = su3.Lattice([8, 8, 8, 8], beta=5.8, seed=21, storage=su3.SU3_FP64_18, start=su3.SU3_START_HOT, hits=2)
+    lat.sweep(3)
+    b0, d0 = lat.action()
+    lat.autotune()
+    b1, d1 = lat.action()
+    assert d1 == d0 and b1 == pytest.approx(b0, rel=1e-15)
+    lat.sweep(2)
+    b2, d2 = lat.action()
+    assert b2 == pytest.approx(d2, rel=1e-11)
