@@ -183,6 +183,12 @@ su3_status su3_measurement_latest_async(su3_lattice *lat, double *host_out, size
 /* Wait until all work queued on the lattice's stream has finished. */
 su3_status su3_synchronize(su3_lattice *lat);
 
+/* The same with a deadline (a host-side watchdog): polls an event recorded
+ * behind the queued work and returns SU3_ETIMEOUT once timeout_s seconds
+ * have passed; the work keeps running and a later call can wait again.
+ * EINVAL for a negative timeout. */
+su3_status su3_wait(su3_lattice *lat, double timeout_s);
+
 /* Copy all links to / from the host in the canonical layout; n is the
  * number of doubles in the host buffer (>= 18 * links).  set_links rounds
  * to the storage precision (FP32_12 keeps rows 1 and 2, FP32_18 rounds all
@@ -334,6 +340,8 @@ su3_status su3_ensemble_create(const su3_config *cfgs, int nchains, void *stream
 void su3_ensemble_destroy(su3_ensemble *ens);
 /* n sweeps of every chain (hits from each config). */
 su3_status su3_ensemble_sweep(su3_ensemble *ens, int n);
+/* su3_wait for an ensemble: the queued work, with a deadline (ETIMEOUT). */
+su3_status su3_ensemble_wait(su3_ensemble *ens, double timeout_s);
 /* Plaquette and Polyakov loop of every chain, whole lattice: out[5*c + k],
  * k = total, space, time, poly_re, poly_im.  Synchronises. */
 su3_status su3_ensemble_measure(su3_ensemble *ens, double *host_out);

@@ -35,7 +35,7 @@ SU3_LINKS_FP64_18, SU3_LINKS_FP32_12 = 0, 1
 EXPORTED = [
     "su3_config_init", "su3_link_bytes", "su3_lattice_create", "su3_lattice_create_ex", "su3_lattice_destroy",
     "su3_sweep", "su3_reunitarize", "su3_plaquette", "su3_polyakov", "su3_measure_async", "su3_measurements",
-    "su3_get_links", "su3_set_links", "su3_stage_links", "su3_stage_links_ex", "su3_apply_links", "su3_measurement_latest", "su3_measurement_latest_async", "su3_synchronize", "su3_stats", "su3_action", "su3_action_reset", "su3_set_sweep_counter", "su3_lattice_info", "su3_set_launch",
+    "su3_get_links", "su3_set_links", "su3_stage_links", "su3_stage_links_ex", "su3_apply_links", "su3_measurement_latest", "su3_measurement_latest_async", "su3_synchronize", "su3_wait", "su3_ensemble_wait", "su3_stats", "su3_action", "su3_action_reset", "su3_set_sweep_counter", "su3_lattice_info", "su3_set_launch",
     "su3_autotune", "su3_use_graph", "su3_use_pdl", "su3_set_profiling", "su3_get_profile", "su3_ensemble_create", "su3_ensemble_destroy", "su3_ensemble_sweep",
     "su3_ensemble_measure", "su3_ensemble_get_links", "su3_ensemble_measurements", "su3_ensemble_set_launch", "su3_ensemble_autotune", "su3_ensemble_use_graph",
     "su3_ensemble_set_profiling", "su3_ensemble_get_profile",
@@ -111,6 +111,8 @@ def lib():
             "su3_measurement_latest": (c_int, [vp, dp, sz]),
             "su3_measurement_latest_async": (c_int, [vp, dp, sz]),
             "su3_synchronize": (c_int, [vp]),
+            "su3_wait": (c_int, [vp, c_double]),
+            "su3_ensemble_wait": (c_int, [vp, c_double]),
             "su3_apply_links": (c_int, [vp]),
             "su3_stats": (c_int, [vp, u64p, u64p, u64p]),
             "su3_set_sweep_counter": (c_int, [vp, c_uint64]),
@@ -272,6 +274,14 @@ def su3_synchronize(h):
     _check(lib().su3_synchronize(h))
 
 
+def su3_wait(h, timeout_s: float):
+    _check(lib().su3_wait(h, float(timeout_s)))
+
+
+def su3_ensemble_wait(h, timeout_s: float):
+    _check(lib().su3_ensemble_wait(h, float(timeout_s)))
+
+
 def su3_stats(h):
     p, a, s = c_uint64(), c_uint64(), c_uint64()
     _check(lib().su3_stats(h, byref(p), byref(a), byref(s)))
@@ -339,6 +349,22 @@ def su3_last_error() -> str:
 
 def su3_version() -> str:
     return lib().su3_version().decode()
+
+
+def _tuned(h, cfgs, cache, run, apply):
+    """Autotune through the launch-shape cache (paper_0904_0642_gb300.tuning)."""
+    from . import tuning
+    path = cache or os.environ.get("SU3_TUNE_CACHE")
+    if not path:
+        return run(h)
+    key = tuning.key_of(cfgs, su3_version())
+    hit = tuning.lookup(path, key)
+    if hit is not None:
+        apply(hit[0], hit[1], hit[2])
+        return hit
+    shape = run(h)
+    tuning.store(path, key, shape)
+    return shape
 
 
 # ---------------------------------------------------------------- classes
@@ -460,6 +486,11 @@ class Lattice:
     def synchronize(self):
         su3_synchronize(self.h)
 
+    def wait(self, timeout_s: float):
+        """Wait for the queued work at most timeout_s seconds (Su3Error with
+        SU3_ETIMEOUT after that; the work keeps running)."""
+        su3_wait(self.h, timeout_s)
+
     def apply_links(self):
         su3_apply_links(self.h)
 
@@ -483,8 +514,12 @@ class Lattice:
     def set_launch(self, threads, ctas_per_sm=0, variant=0):
         su3_set_launch(self.h, variant, threads, ctas_per_sm)
 
-    def autotune(self):
-        return su3_autotune(self.h)
+    def autotune(self, cache: str | None = None):
+        """Time the launch shapes and keep the fastest: (variant, threads,
+        ctas_per_sm, us_per_sweep).  cache (or $SU3_TUNE_CACHE): a JSON
+        file of earlier results for the same shape class; a hit is applied
+        without timing, a miss is timed and stored."""
+        return _tuned(self.h, [self.cfg], cache, su3_autotune, lambda v, t, c: su3_set_launch(self.h, v, t, c))
 
     def use_graph(self, on=True):
         su3_use_graph(self.h, on)
@@ -524,6 +559,9 @@ class Ensemble:
     def sweep(self, n=1):
         _check(lib().su3_ensemble_sweep(self.h, n))
 
+    def wait(self, timeout_s: float):
+        su3_ensemble_wait(self.h, timeout_s)
+
     def measure(self) -> np.ndarray:
         out = np.zeros((self.n, 5), dtype=np.float64)
         _check(lib().su3_ensemble_measure(self.h, _dp(out)))
@@ -548,10 +586,17 @@ class Ensemble:
     def set_launch(self, threads, ctas_per_sm=0, variant=0):
         _check(lib().su3_ensemble_set_launch(self.h, variant, threads, ctas_per_sm))
 
-    def autotune(self):
-        v, t, c, us = c_int(), c_int(), c_int(), c_double()
-        _check(lib().su3_ensemble_autotune(self.h, byref(v), byref(t), byref(c), byref(us)))
-        return v.value, t.value, c.value, us.value
+    def autotune(self, cache: str | None = None):
+        """As Lattice.autotune, for the fused launch of all chains."""
+        def run(h):
+            v, t, c, us = c_int(), c_int(), c_int(), c_double()
+            _check(lib().su3_ensemble_autotune(h, byref(v), byref(t), byref(c), byref(us)))
+            return v.value, t.value, c.value, us.value
+
+        def apply(v, t, c):
+            _check(lib().su3_ensemble_set_launch(self.h, v, t, c))
+
+        return _tuned(self.h, self.cfgs, cache, run, apply)
 
     def use_graph(self, on=True):
         _check(lib().su3_ensemble_use_graph(self.h, int(bool(on))))

@@ -19,9 +19,21 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/su3.h"
 #include "su3_engine.h"
 #include "su3_launch.h"
+
+namespace {
+// NVTX range for profilers (a no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 using namespace su3g;
 
@@ -432,9 +444,28 @@ struct Engine {
     return SU3_OK;
   }
 
+  // Host-side watchdog: wait for the work queued so far, polling an event
+  // with a deadline (ETIMEOUT when it passes; the work keeps running).
+  cudaEvent_t wait_event = nullptr;
+  su3_status wait_for(double timeout_s) {
+    if (!wait_event) CU(cudaEventCreateWithFlags(&wait_event, cudaEventDisableTiming));
+    CU(cudaEventRecord(wait_event, stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      const cudaError_t q = cudaEventQuery(wait_event);
+      if (q == cudaSuccess) return SU3_OK;
+      if (q != cudaErrorNotReady) return fail(SU3_ECUDA, "cudaEventQuery: %s", cudaGetErrorString(q));
+      const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (dt >= timeout_s) return fail(SU3_ETIMEOUT, "queued work not finished after %g s", timeout_s);
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+  }
+
   void release() {
     if (stream) cudaStreamSynchronize(stream);
     drop_events();
+    if (wait_event) cudaEventDestroy(wait_event);
+    wait_event = nullptr;
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
     for (auto &ch : chains) free_chain(ch);
@@ -1070,6 +1101,7 @@ extern "C" void su3_lattice_destroy(su3_lattice *lat) { delete lat; }
 
 extern "C" su3_status su3_sweep(su3_lattice *lat, int n, int hits) {
   LAT_CHECK(lat);
+  NvtxRange r("su3_sweep");
   if (hits < 1 || hits > 254) return fail(SU3_EINVAL, "hits=%d outside 1..254", hits);
   Chain &ch = lat->eng.chains[0];
   if (ch.cfg.hits != hits) {
@@ -1191,6 +1223,12 @@ extern "C" su3_status su3_synchronize(su3_lattice *lat) {
   LAT_CHECK(lat);
   CU(cudaStreamSynchronize(lat->eng.stream));
   return SU3_OK;
+}
+
+extern "C" su3_status su3_wait(su3_lattice *lat, double timeout_s) {
+  LAT_CHECK(lat);
+  if (!(timeout_s >= 0.0)) return fail(SU3_EINVAL, "timeout %g s must be >= 0", timeout_s);
+  return lat->eng.wait_for(timeout_s);
 }
 
 extern "C" su3_status su3_get_links(su3_lattice *lat, double *host, size_t n) {
@@ -1502,7 +1540,14 @@ extern "C" void su3_ensemble_destroy(su3_ensemble *ens) { delete ens; }
 
 extern "C" su3_status su3_ensemble_sweep(su3_ensemble *ens, int n) {
   if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
+  NvtxRange r("su3_ensemble_sweep");
   return ens->eng.sweep_all(n);
+}
+
+extern "C" su3_status su3_ensemble_wait(su3_ensemble *ens, double timeout_s) {
+  if (!ens) return fail(SU3_EINVAL, "ensemble handle is NULL");
+  if (!(timeout_s >= 0.0)) return fail(SU3_EINVAL, "timeout %g s must be >= 0", timeout_s);
+  return ens->eng.wait_for(timeout_s);
 }
 
 extern "C" su3_status su3_ensemble_measure(su3_ensemble *ens, double *host_out) {
@@ -1779,6 +1824,7 @@ void su3_server::loop() {
     }
     if (eng.chains.empty()) continue;
     // One round of fused ticks for every resident chain.
+    NvtxRange round("su3_server_round");
     if (eng.run_ticks(kTicksPerRound) != SU3_OK || eng.download_states() != SU3_OK) {
       worker_error = g_err;
       break;

@@ -206,3 +206,38 @@ def test_two_coupling_chain_in_ensemble_leaves_others_bitwise():
                             seed=cfg.seed, storage=cfg.storage, start=cfg.start, hits=cfg.hits)
         alone.sweep(4)
         assert np.array_equal(ens.get_links(i), alone.get_links()), i
+
+
+def test_autotune_cache(tmp_path):
+    """A cached launch shape is applied without timing, and gives the same
+    links as any other shape."""
+    import time
+    path = str(tmp_path / "tune.json")
+    kw = dict(beta=6.0, seed=4, storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT, reunit_every=5)
+    a = su3.Lattice([16, 16, 16, 16], **kw)
+    first = a.autotune(cache=path)
+    b = su3.Lattice([16, 16, 16, 16], **kw)
+    t0 = time.perf_counter()
+    second = b.autotune(cache=path)
+    assert second == first and time.perf_counter() - t0 < 0.5
+    a.sweep(3)
+    b.sweep(3)
+    assert np.array_equal(a.get_links(), b.get_links())
+
+
+def test_wait_with_deadline():
+    """Host watchdog: a deadline that passes before the queued work ends
+    gives SU3_ETIMEOUT and leaves the work running; a later wait succeeds."""
+    lat = su3.Lattice([32, 32, 32, 32], beta=6.0, seed=1, storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT,
+                      reunit_every=10)
+    lat.sweep(1)
+    lat.synchronize()
+    lat.sweep(40)  # ~30 ms queued
+    with pytest.raises(su3.Su3Error) as ei:
+        lat.wait(0.0)
+    assert ei.value.status == su3.SU3_ETIMEOUT
+    lat.wait(120.0)
+    assert lat.stats()[2] == 41
+    with pytest.raises(su3.Su3Error) as ei:
+        lat.wait(-1.0)
+    assert ei.value.status == su3.SU3_EINVAL
