@@ -307,7 +307,9 @@ su3_status su3_get_profile(su3_lattice *lat, su3_profile *out, int reset);
  * fixed device-memory budget.
  *
  * cfg:        geometry and storage of the links (D, dims, boundary,
- *             glue_mask, storage); the other fields are ignored.
+ *             glue_mask, storage): only these fields are read and
+ *             validated; every other field is ignored (a zero-filled
+ *             struct with these five set is accepted).
  * links:      device pointer to link storage in the library's layout,
  *             16-byte aligned (e.g. the caller-owned link_buffer a lattice
  *             was created with).
@@ -317,16 +319,20 @@ su3_status su3_get_profile(su3_lattice *lat, su3_profile *out, int reset);
  * stream:     cudaStream_t (NULL: the legacy default stream); asynchronous.
  *
  * Scratch: the per-block partial sums go to a fixed 1 MiB array inside the
- * library (32768 slots, one per 256 sites of one colour and layer), which
- * every GPU that loads the library holds until the process exits.  A lattice
- * that needs more slots (more than 8,388,608 sites of one colour summed over
- * its layers) is rejected with SU3_EINVAL before anything is launched.  Each
- * call writes every slot it reads, so nothing needs clearing between calls,
- * but all calls share the one array: calls that overlap on the GPU (other
- * streams, other threads) race, so serialise them.
+ * library (32768 slots), which every GPU that loads the library holds until
+ * the process exits.  A lattice needs one slot per tile of 256 sites of one
+ * colour in each layer: layers x ceil(V / 2 / 256) slots, V the sites of one
+ * layer (each layer's count is rounded up to whole tiles).  A lattice that
+ * needs more than 32768 slots (64^4 PBC needs exactly 32768) is rejected
+ * with SU3_EINVAL before anything is launched.  Each call writes every slot
+ * it reads, so nothing needs clearing between calls, but all calls share
+ * the one array: calls that overlap on the GPU (other streams, other
+ * threads) race, so serialise them.
  * Set-up: the first call on each device looks up the device address of the
- * array (cudaGetSymbolAddress) and keeps it; make that first call on a
- * device before any stream capture. */
+ * array (cudaGetSymbolAddress) and keeps it with the id of the current
+ * context; a later call in another context of that device (after
+ * cudaDeviceReset, say) looks it up again.  Make the first call on a
+ * device, and the first after a reset, before any stream capture. */
 su3_status su3_measure_noalloc(const su3_config *cfg, const void *links, double *device_out, void *stream);
 
 /* ---------------------------------------------------------------- ensembles

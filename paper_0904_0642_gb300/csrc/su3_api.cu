@@ -83,7 +83,9 @@ extern "C" void su3_config_init(su3_config *c) {
   c->beta1 = -1.0;
 }
 
-static su3_status validate(const su3_config *c) {
+// The fields that fix the shape and layout of a chain's links: D, the
+// extents, the boundary, the glued directions and the storage form.
+static su3_status validate_geometry(const su3_config *c) {
   if (!c) return fail(SU3_EINVAL, "config is NULL");
   if (c->D < 2 || c->D > SU3_MAX_D) return fail(SU3_EINVAL, "D=%d outside 2..%d", c->D, SU3_MAX_D);
   long long V = 1;
@@ -91,23 +93,31 @@ static su3_status validate(const su3_config *c) {
     if (c->dims[i] < 2 || (c->dims[i] & 1))
       return fail(SU3_EINVAL, "extent n^%d=%d: the checkerboard needs even extents >= 2", i + 1, c->dims[i]);
     V *= c->dims[i];
-    const int p = c->rng_period[i];
-    if (p != 0 && (p < 2 || (p & 1) || c->dims[i] % p))
-      return fail(SU3_EINVAL, "rng_period[%d]=%d must be even and divide n^%d=%d", i, p, i + 1, c->dims[i]);
   }
   const int layers = c->boundary == SU3_DLT ? 2 : 1;
   if (c->boundary != SU3_PBC && c->boundary != SU3_DLT) return fail(SU3_EINVAL, "unknown boundary %d", c->boundary);
   if (V * layers * c->D * 9 >= 0x7fffffffLL)
     return fail(SU3_EINVAL, "lattice too large: link storage must stay below 2^31 vectors");
+  if (c->storage != SU3_FP64_18 && c->storage != SU3_FP32_12 && c->storage != SU3_FP32_18)
+    return fail(SU3_EINVAL, "unknown storage %d", c->storage);
+  if (c->glue_mask < 0 || c->glue_mask >= (1 << c->D)) return fail(SU3_EINVAL, "glue_mask=%d out of range", c->glue_mask);
+  return SU3_OK;
+}
+
+static su3_status validate(const su3_config *c) {
+  TRY(validate_geometry(c));
+  for (int i = 0; i < c->D; ++i) {
+    const int p = c->rng_period[i];
+    if (p != 0 && (p < 2 || (p & 1) || c->dims[i] % p))
+      return fail(SU3_EINVAL, "rng_period[%d]=%d must be even and divide n^%d=%d", i, p, i + 1, c->dims[i]);
+  }
+  const int layers = c->boundary == SU3_DLT ? 2 : 1;
   if (!(c->beta >= 0.0) || !std::isfinite(c->beta)) return fail(SU3_EINVAL, "beta=%g must be finite and >= 0", c->beta);
   if (!std::isfinite(c->beta1)) return fail(SU3_EINVAL, "beta1=%g must be finite (< 0: equal to beta)", c->beta1);
   if (c->hits < 1 || c->hits > 254) return fail(SU3_EINVAL, "hits=%d outside 1..254", c->hits);
-  if (c->storage != SU3_FP64_18 && c->storage != SU3_FP32_12 && c->storage != SU3_FP32_18)
-    return fail(SU3_EINVAL, "unknown storage %d", c->storage);
   if (c->start != SU3_START_COLD && c->start != SU3_START_HOT) return fail(SU3_EINVAL, "unknown start %d", c->start);
   if (c->reunit_every < 0 || c->measure_every < 0 || c->measure_capacity < 0)
     return fail(SU3_EINVAL, "negative cadence or capacity");
-  if (c->glue_mask < 0 || c->glue_mask >= (1 << c->D)) return fail(SU3_EINVAL, "glue_mask=%d out of range", c->glue_mask);
   long long Vbox = 1;
   for (int i = 0; i < SU3_MAX_D; ++i) {
     const int k = c->ndiv[i];
@@ -1479,13 +1489,21 @@ extern "C" su3_status su3_autotune(su3_lattice *lat, int *variant, int *threads,
 
 extern "C" su3_status su3_measure_noalloc(const su3_config *cfg, const void *links, double *device_out,
                                           void *stream) {
-  TRY(validate(cfg));
+  TRY(validate_geometry(cfg));  // only these fields are read
   if (!links || ((uintptr_t)links & 15)) return fail(SU3_EINVAL, "links must be a 16-byte aligned device pointer");
   if (!device_out) return fail(SU3_EINVAL, "device_out is NULL");
   const int block = 256;
   Chain ch;  // a descriptor only: no device memory is touched or allocated here
-  ch.cfg = *cfg;
-  for (int i = 0; i < SU3_MAX_D; ++i) ch.cfg.ndiv[i] = 0;  // the caller's links are undivided
+  // The descriptor is built from the geometry and storage alone, so that
+  // every other field of *cfg is ignored as documented (the caller's links
+  // are undivided; cadences, couplings and random-number periods play no
+  // part in a measurement).
+  su3_config_init(&ch.cfg);
+  ch.cfg.D = cfg->D;
+  for (int i = 0; i < SU3_MAX_D; ++i) ch.cfg.dims[i] = cfg->dims[i];
+  ch.cfg.boundary = cfg->boundary;
+  ch.cfg.glue_mask = cfg->glue_mask;
+  ch.cfg.storage = cfg->storage;
   ch.links = const_cast<void *>(links);
   fill_desc(ch, block);
   const long long tiles = (long long)ch.desc.tiles_per_layer * ch.desc.nlayers;

@@ -721,4 +721,100 @@ __device__ __forceinline__ void cm_update(M3<R> &U, const M3<R> &A, R beta, int 
   }
 }
 
+// ------------------------------------------------------------------ Cabibbo-Marinari, float, draws first
+// The random numbers of the first proposal and of the direction of every
+// subgroup do not depend on the staple: they are functions of the counter
+// alone.  So are the parts of the proposal and of the direction that do not
+// involve alpha: L = ln u1 + cos^2(2 pi u2) ln u3 (X = -L / alpha), u4^2,
+// and cos(theta), sin(theta), cos(phi), sin(phi).  cm_update_f computes
+// them for all three subgroups before the sequential part, as six
+// independent Philox chains that the scheduler can interleave; each
+// subgroup then runs only the alpha-dependent steps.  The arithmetic and its
+// order are those of su2_draw_f<false>; rejected first proposals (further
+// hits) and the rare alpha ranges (alpha < 2: accurate logarithms,
+// alpha >= 32: double precision) take su2_draw as before.
+struct DrawPre {
+  float L, u4sq, costh, sinth, cphi, sphi;
+};
+
+__device__ __forceinline__ DrawPre draw_pre_f(uint2 key, uint32_t c0, uint32_t c1, uint32_t tag) {
+  DrawPre p;
+  const uint4 w = philox4x32_10(make_uint4(c0, c1, tag, kPurposeHeatbath), key);
+  const float ang = __fmaf_rn(unif_f(w.y), 6.28318530717958648f, -3.14159265358979324f);
+  const float cs = __cosf(ang);
+  const float l1 = __logf(unif_f(w.x));
+  const float l3 = __logf(unif_f(w.z));
+  p.L = l1 + cs * cs * l3;
+  const float u4 = unif_f(w.w);
+  p.u4sq = u4 * u4;
+  const uint4 v = philox4x32_10(make_uint4(c0, c1, tag | kHitDirection, kPurposeHeatbath), key);
+  p.costh = 2.0f * unif_f(v.x) - 1.0f;
+  p.sinth = sqrt_sfu(1.0f - p.costh * p.costh);
+  float sphi, cphi;
+  __sincosf(__fmaf_rn(unif_f(v.y), 6.28318530717958648f, -3.14159265358979324f), &sphi, &cphi);
+  p.sphi = -sphi;  // sin(2 pi u) = -sin(2 pi (u - 1/2)), likewise cos
+  p.cphi = -cphi;
+  return p;
+}
+
+// The float draw of one subgroup from its precomputed first proposal.
+__device__ __forceinline__ bool su2_draw_pre(float alpha, int hits, uint2 key, uint32_t c0, uint32_t c1, uint32_t tag,
+                                             const DrawPre &p, float x[4], uint32_t &nprop) {
+  if (alpha >= kAlphaFp64 || alpha < kAlphaAccurateLog) return su2_draw(alpha, hits, key, c0, c1, tag, x, nprop);
+  const float ia = rcp_sfu(alpha);
+  ++nprop;
+  float X = -p.L * ia;
+  bool acc = p.u4sq <= 1.0f - 0.5f * X;
+  for (int h = 1; h < hits && !acc; ++h) {
+    const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | (uint32_t)h, kPurposeHeatbath), key);
+    ++nprop;
+    const float ang = __fmaf_rn(unif_f(w.y), 6.28318530717958648f, -3.14159265358979324f);
+    const float cs = __cosf(ang);
+    const float l1 = __logf(unif_f(w.x));
+    const float l3 = __logf(unif_f(w.z));
+    X = -(l1 + cs * cs * l3) * ia;
+    const float u4 = unif_f(w.w);
+    acc = u4 * u4 <= 1.0f - 0.5f * X;
+  }
+  if (!acc) return false;
+  const float rho = sqrt_sfu(X * (2.0f - X));
+  x[0] = 1.0f - X;
+  x[1] = rho * p.sinth * p.cphi;
+  x[2] = rho * p.sinth * p.sphi;
+  x[3] = rho * p.costh;
+  return true;
+}
+
+// cm_update for float links with the draws' counter-only parts first.
+__device__ __forceinline__ void cm_update_f(M3<float> &U, const M3<float> &A, float beta, int hits, uint2 key,
+                                            uint32_t c0, uint32_t c1, int colour, int mu, uint32_t &nprop,
+                                            uint32_t &nacc, float &dretr) {
+  DrawPre pre[3];
+#pragma unroll
+  for (int sg = 0; sg < 3; ++sg) pre[sg] = draw_pre_f(key, c0, c1, heatbath_tag(colour, mu, sg));
+  dretr = 0.0f;
+  const float ca = 2.0f * beta / 3.0f;
+#pragma unroll
+  for (int sg = 0; sg < 3; ++sg) {
+    const int i = (sg == 2) ? 1 : 0;
+    const int j = (sg == 0) ? 1 : 2;
+    float a0, a1, a2, a3;
+    block_projection(U, A, i, j, a0, a1, a2, a3);
+    float k, ik;
+    norm_and_inverse(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3, k, ik);
+    if (!(k > 1e-30f)) continue;
+    const float alpha = ca * k;
+    float x[4];
+    if (!su2_draw_pre(alpha, hits, key, c0, c1, heatbath_tag(colour, mu, sg), pre[sg], x, nprop)) continue;
+    ++nacc;
+    dretr += 2.0f * (k * x[0] - a0);
+    const float v0 = a0 * ik, v1 = a1 * ik, v2 = a2 * ik, v3 = a3 * ik;
+    const float r0 = x[0] * v0 + x[1] * v1 + x[2] * v2 + x[3] * v3;
+    const float r1 = -x[0] * v1 + v0 * x[1] + (x[2] * v3 - x[3] * v2);
+    const float r2 = -x[0] * v2 + v0 * x[2] + (x[3] * v1 - x[1] * v3);
+    const float r3 = -x[0] * v3 + v0 * x[3] + (x[1] * v2 - x[2] * v1);
+    rotate_rows(U, i, j, r0, r1, r2, r3);
+  }
+}
+
 }  // namespace su3g

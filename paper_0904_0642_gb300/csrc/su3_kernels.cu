@@ -10,6 +10,9 @@
 //   conversion and stand-alone measurements.
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
+
+#include <cuda.h>  // CUcontext / CUresult for the two driver calls reached through the runtime
 
 #include "su3_device.cuh"
 #include "su3_launch.h"
@@ -215,6 +218,110 @@ __device__ __forceinline__ void add_staples(const ChainDesc &d, const SiteGeo &g
     acc_su3_2rows(A, mul_dn_2(ef, h));
 }
 
+// The staples of one direction nu from precomputed plane offsets (p*, in
+// vectors from the chain's link base) and checkerboard indices (j*) of the
+// six links: the arithmetic and its order are those of add_staples.  Plane
+// offset and index stay separate because the 18-real float form addresses a
+// plane's 16-byte vectors from its (16-byte aligned) start.
+// Where a form's vectors are its addressing unit (every form but the 18-real
+// float one) offset and index are summed first: one index per link.
+template <class S>
+__device__ __forceinline__ M3<typename S::R> load_at(const typename S::Vec *base, int Vh, int p, int j, bool rows2) {
+  if constexpr (std::is_same<S, StoreF32x18>::value)
+    return rows2 ? S::load2(base + p, Vh, j) : S::load(base + p, Vh, j);
+  else
+    return rows2 ? S::load2(base + (p + j), Vh, 0) : S::load(base + (p + j), Vh, 0);
+}
+
+template <class S, bool WT>
+__device__ __forceinline__ void add_staples_idx(const ChainDesc &d, const typename S::Vec *base, int Vh, int pb, int jb,
+                                                int pc, int jc, int pa, int ja, int pf, int jf, int pe, int je, int ph,
+                                                int jh, int wu, int wl, M3<typename S::R> &A) {
+  using R = typename S::R;
+  const M3<R> b = load_at<S>(base, Vh, pb, jb, false);  // U_mu(x+nu)
+  const M3<R> c = load_at<S>(base, Vh, pc, jc, true);   // U_nu(x)
+  M3<R> cb = mul_nn_2(c, b);
+  third_row(cb);
+  const M3<R> a = load_at<S>(base, Vh, pa, ja, true);   // U_nu(x+mu)
+  const bool weighted = WT && d.weighted;
+  const R b0 = sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d, b1 = sizeof(R) == 4 ? (R)d.beta1_f : (R)d.beta1_d;
+  if (weighted)
+    acc_su3_2rows_w(A, mul_nd_2(a, cb), wu ? b1 : b0);
+  else
+    acc_su3_2rows(A, mul_nd_2(a, cb));
+  const M3<R> f = load_at<S>(base, Vh, pf, jf, false);  // U_nu(x+mu-nu)
+  const M3<R> e = load_at<S>(base, Vh, pe, je, true);   // U_mu(x-nu)
+  M3<R> ef = mul_nn_2(e, f);
+  third_row(ef);
+  const M3<R> h = load_at<S>(base, Vh, ph, jh, false);  // U_nu(x-nu)
+  if (weighted)
+    acc_su3_2rows_w(A, mul_dn_2(ef, h), wl ? b1 : b0);
+  else
+    acc_su3_2rows(A, mul_dn_2(ef, h));
+}
+
+// update_site for an undivided lattice with the neighbour geometry computed
+// once per site: forward and backward site offsets and layer flips in every
+// direction, and the plane offsets as multiples of one plane stride.  Same
+// arithmetic, same order as update_site.
+template <class S, bool WT>
+__device__ __forceinline__ void update_site_lean(const ChainDesc &d, uint32_t sweep, int colour, int mu, int layer,
+                                                 int jj, uint32_t &nprop, uint32_t &nacc, typename S::R &dretr) {
+  using R = typename S::R;
+  using Vec = typename S::Vec;
+  const int Vh = d.Vh, D = d.D;
+  const SiteGeo g = site_of<false>(d, layer, colour, jj);
+  const int PS = S::NQ * Vh, CS = D * PS, LS = 2 * CS;
+  const int oc = colour ^ 1;
+  const Vec *base = reinterpret_cast<const Vec *>(d.links);
+  const int s = g.s;
+  int of[kMaxD], ob[kMaxD], ff[kMaxD], fb[kMaxD];
+#pragma unroll
+  for (int k = 0; k < kMaxD; ++k) {
+    of[k] = ob[k] = ff[k] = fb[k] = 0;
+    if (k < D) {
+      step_fwd(d, g.x[k], k, of[k], ff[k]);
+      step_bwd(d, g.x[k], k, ob[k], fb[k]);
+    }
+  }
+  int ofm = 0, ffm = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxD; ++k)
+    if (k == mu) {
+      ofm = of[k];
+      ffm = ff[k];
+    }
+  const int lp = layer ^ ffm;            // layer of x + mu
+  const int sp = s + ofm;                // x + mu
+  const int pmu_oc = oc * CS + mu * PS;  // plane (oc, mu) within a layer
+  const uint2 key = make_uint2(d.seed_lo, d.seed_hi);
+  const uint32_t skey = site_key<false>(d, g);
+  M3<R> A = m3_zero<R>();
+#pragma unroll
+  for (int nu = 0; nu < kMaxD; ++nu) {
+    if (nu < D && nu != mu) {
+      const int lb = layer ^ ff[nu], lm = layer ^ fb[nu], lf = lp ^ fb[nu];
+      const int sm = s + ob[nu];
+      add_staples_idx<S, WT>(d, base, Vh,
+                             lb * LS + pmu_oc, (s + of[nu]) >> 1,                   // U_mu(x+nu)
+                             layer * LS + colour * CS + nu * PS, jj,                // U_nu(x)
+                             lp * LS + oc * CS + nu * PS, sp >> 1,                  // U_nu(x+mu)
+                             lf * LS + colour * CS + nu * PS, (sp + ob[nu]) >> 1,   // U_nu(x+mu-nu)
+                             lm * LS + pmu_oc, sm >> 1,                             // U_mu(x-nu)
+                             lm * LS + oc * CS + nu * PS, sm >> 1,                  // U_nu(x-nu)
+                             layer | lp | lb, lm | lf | layer, A);
+    }
+  }
+  typename S::Vec *pu = plane_ptr<S>(d, layer, colour, mu);
+  M3<R> U = S::load(pu, Vh, jj);
+  const R beta = (WT && d.weighted) ? R(1) : (sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d);
+  if constexpr (sizeof(R) == 4)
+    cm_update_f(U, A, beta, d.hits, key, skey, sweep, colour, mu, nprop, nacc, dretr);
+  else
+    cm_update(U, A, beta, d.hits, key, skey, sweep, colour, mu, nprop, nacc, dretr);
+  S::store(pu, Vh, jj, U);
+}
+
 // ROLLED: the loop over staple directions stays a loop (no unrolling), so the
 // compiler cannot hoist later directions' loads; fewer registers, less code.
 template <class S, bool ROLLED, bool WT, bool SUB>
@@ -243,7 +350,10 @@ __device__ __forceinline__ void update_site(const ChainDesc &d, uint32_t sweep, 
   const int ju = g.s >> 1;  // jj itself unless the site sits in a padded box
   M3<R> U = S::load(pu, Vh, ju);
   const R beta = (WT && d.weighted) ? R(1) : (sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d);
-  cm_update(U, A, beta, d.hits, key, skey, sweep, colour, mu, nprop, nacc, dretr);
+  if constexpr (sizeof(R) == 4)
+    cm_update_f(U, A, beta, d.hits, key, skey, sweep, colour, mu, nprop, nacc, dretr);
+  else
+    cm_update(U, A, beta, d.hits, key, skey, sweep, colour, mu, nprop, nacc, dretr);
   S::store(pu, Vh, ju, U);
 }
 
@@ -571,7 +681,12 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
     if (ss.stage < 2 * sd.D) {
       const int colour = ss.stage / sd.D, mu = ss.stage - colour * sd.D;
       typename S::R dr = 0;  // change of Re Tr(U A), in the kernel's precision
-      if (valid) update_site<S, TickBounds<V>::kRolled, WT, SUB>(sd, ss.sweep, colour, mu, layer, jj, np, na, dr);
+      if (valid) {
+        if constexpr (!TickBounds<V>::kRolled && !SUB)
+          update_site_lean<S, WT>(sd, ss.sweep, colour, mu, layer, jj, np, na, dr);
+        else
+          update_site<S, TickBounds<V>::kRolled, WT, SUB>(sd, ss.sweep, colour, mu, layer, jj, np, na, dr);
+      }
       // book the action change S = sum_p beta_p (1 - Re Tr U_p / 3): each warp
       // owns the slot of its 32 sites, so the one fire-and-forget add per warp
       // meets no other add in this launch and the order of adds is fixed
@@ -1008,23 +1123,61 @@ __global__ void k_measure_finalize_noalloc(ChainDesc d, const double *partials, 
 
 int noalloc_max_tiles() { return kNoAllocTiles; }
 
-// Device address of the scratch array on the current device.  Host code
+// The unique id of the current context (cuCtxGetId), or 0 when there is no
+// current context or the driver cannot say.  The two driver calls are
+// reached through the runtime's entry-point table, so the library does not
+// link the driver library itself.
+static unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(p);
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context.  Host code
 // cannot use the symbol itself (it names a host-side stand-in), so the
-// address is looked up once per device and cached.
+// address is looked up with cudaGetSymbolAddress.  It is kept per device
+// together with the id of the context it was taken in: a device reset
+// (cudaDeviceReset) or any other teardown of the context unloads the
+// library's module, and the next call then sees a new context id and looks
+// the address up again instead of using a stale one.  Without a context id
+// the address is looked up on every call.
 static cudaError_t noalloc_scratch(double **ptr) {
   static std::mutex mu;
   static double *addr[64] = {nullptr};
+  static unsigned long long ctx_of[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess) return e;
-    addr[dev] = static_cast<double *>(p);
+  const unsigned long long id = current_context_id();
+  if (id && ctx_of[dev] == id && addr[dev]) {
+    *ptr = addr[dev];
+    return cudaSuccess;
   }
+  void *p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_partials);  // also makes the device's context current
+  if (e != cudaSuccess) return e;
+  addr[dev] = static_cast<double *>(p);
+  ctx_of[dev] = current_context_id();
   *ptr = addr[dev];
   return cudaSuccess;
 }
