@@ -372,6 +372,15 @@ typedef struct su3_server su3_server;
 typedef struct su3_job {
   su3_config cfg;          /* lattice of the job (stream and link_buffer ignored) */
   int32_t sweeps;          /* sweeps to run, >= 1 */
+  /* Optional host buffers (NULL: unused), each layers*V*D*18 doubles in the
+   * canonical layout of su3_get_links, owned by the caller and read or
+   * written by the server's worker thread: they must stay valid until the
+   * job's result has been collected (su3_server_poll / su3_server_wait).
+   * links_in:  start configuration, replacing cfg.start (written at
+   *            admission, as su3_set_links would).
+   * links_out: receives the links after the last sweep, at retirement. */
+  const double *links_in;
+  double *links_out;
 } su3_job;
 
 typedef struct su3_result {
@@ -386,19 +395,41 @@ typedef struct su3_result {
 } su3_result;
 
 /* hbm_budget_bytes: device bytes the resident chains may hold (0: 80 % of
- * free memory); max_slots: resident chains at most. */
+ * free memory); max_slots: resident chains at most.
+ * The worker thread runs the resident chains in rounds of 16 fused ticks
+ * (one captured graph) and reads their stage machines back after each
+ * round (one host synchronisation per round): admission and retirement
+ * happen between rounds, which sets the granularity of job latency. */
 su3_status su3_server_create(size_t hbm_budget_bytes, int max_slots, su3_server **out);
 /* Queue a job; never blocks.  EINVAL for a bad job, ENOMEM when the job
- * alone exceeds the budget. */
+ * alone exceeds the budget, ECUDA (with the worker's message) once the
+ * worker has stopped after an error. */
 su3_status su3_server_submit(su3_server *srv, const su3_job *job, uint64_t *job_id);
 /* EBUSY while queued or running, OK with *out filled once done, ENOTFOUND
- * for an unknown (or already collected) id. */
+ * for an unknown (or already collected) id.  A job that fails on its own
+ * (its device allocation at admission, its measurement) is done with that
+ * status in out->status.  When the worker itself has stopped after an
+ * error (a failed launch or synchronisation), every job not yet done gets
+ * ECUDA with the worker's message from poll and wait, instead of EBUSY or
+ * a timeout. */
 su3_status su3_server_poll(su3_server *srv, uint64_t job_id, su3_result *out);
 su3_status su3_server_wait(su3_server *srv, uint64_t job_id, double timeout_s, su3_result *out);
 /* Jobs queued, resident, and finished-but-uncollected. */
 su3_status su3_server_load(su3_server *srv, int *queued, int *resident, int *finished);
 /* Stops the scheduler; jobs still queued or running end with SU3_EBUSY. */
 void su3_server_destroy(su3_server *srv);
+
+/* ---------------------------------------------------------------- fault injection
+ * For tests of the error paths, on the host only (no GPU fault is ever
+ * caused): arm the next `count` passes through `site` to fail as the real
+ * failure would (count 0 disarms).  Sites:
+ *   "server_admit"  the admission of a job fails as its device allocation
+ *                   would (that job is done with SU3_ENOMEM; the worker
+ *                   carries on);
+ *   "server_round"  the worker's next round of ticks fails as a failed
+ *                   launch would (the worker stops; see su3_server_poll).
+ * EINVAL for an unknown site or a negative count. */
+su3_status su3_inject_fault(const char *site, int count);
 
 /* Thread-local message of the last error (empty string if none). */
 const char *su3_last_error(void);

@@ -40,7 +40,7 @@ EXPORTED = [
     "su3_ensemble_measure", "su3_ensemble_get_links", "su3_ensemble_measurements", "su3_ensemble_set_launch", "su3_ensemble_autotune", "su3_ensemble_use_graph",
     "su3_ensemble_set_profiling", "su3_ensemble_get_profile",
     "su3_server_create", "su3_server_submit", "su3_server_poll", "su3_server_wait", "su3_server_load",
-    "su3_server_destroy", "su3_last_error", "su3_version", "su3_measure_noalloc",
+    "su3_server_destroy", "su3_last_error", "su3_version", "su3_measure_noalloc", "su3_inject_fault",
 ]
 
 
@@ -68,7 +68,7 @@ class su3_profile(Structure):
 
 
 class su3_job(Structure):
-    _fields_ = [("cfg", su3_config), ("sweeps", c_int32)]
+    _fields_ = [("cfg", su3_config), ("sweeps", c_int32), ("links_in", c_void_p), ("links_out", c_void_p)]
 
 
 class su3_result(Structure):
@@ -145,6 +145,7 @@ def lib():
             "su3_last_error": (c_char_p, []),
             "su3_version": (c_char_p, []),
             "su3_measure_noalloc": (c_int, [POINTER(su3_config), vp, vp, vp]),
+            "su3_inject_fault": (c_int, [c_char_p, c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -335,6 +336,11 @@ def su3_get_profile(h, reset: bool = False) -> dict:
     p = su3_profile()
     _check(lib().su3_get_profile(h, byref(p), int(bool(reset))))
     return {k: getattr(p, k) for k, _ in su3_profile._fields_}
+
+
+def su3_inject_fault(site: str, count: int = 1):
+    """Arm a host-side failure for tests of the error paths (see include/su3.h)."""
+    _check(lib().su3_inject_fault(site.encode(), int(count)))
 
 
 def su3_measure_noalloc(cfg: su3_config, links_ptr: int, device_out_ptr: int, stream=None):
@@ -617,6 +623,7 @@ class Server:
         h = c_void_p()
         _check(lib().su3_server_create(hbm_budget_bytes, max_slots, byref(h)))
         self.h = h.value
+        self._buffers = {}  # job id -> host link buffers the worker reads or writes
 
     def close(self):
         if getattr(self, "h", None):
@@ -629,12 +636,24 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, cfg: su3_config, sweeps: int) -> int:
+    def submit(self, cfg: su3_config, sweeps: int, links_in: np.ndarray | None = None,
+               links_out: np.ndarray | None = None) -> int:
+        """links_in: start configuration (canonical float64 layout, C-contiguous);
+        links_out: array of the same shape that receives the final links."""
         job = su3_job()
         job.cfg = cfg
         job.sweeps = int(sweeps)
+        keep = []
+        for name, a in (("links_in", links_in), ("links_out", links_out)):
+            if a is not None:
+                if a.dtype != np.float64 or not a.flags.c_contiguous:
+                    raise ValueError(f"{name} must be a C-contiguous float64 array")
+                setattr(job, name, a.ctypes.data)
+                keep.append(a)
         jid = c_uint64()
         _check(lib().su3_server_submit(self.h, byref(job), byref(jid)))
+        if keep:
+            self._buffers[jid.value] = keep
         return jid.value
 
     def poll(self, job_id):
@@ -643,11 +662,13 @@ class Server:
         if st == SU3_EBUSY:
             return None
         _check(st)
+        self._buffers.pop(job_id, None)
         return r
 
     def wait(self, job_id, timeout_s=60.0):
         r = su3_result()
         _check(lib().su3_server_wait(self.h, job_id, timeout_s, byref(r)))
+        self._buffers.pop(job_id, None)
         return r
 
     def load(self):

@@ -6,6 +6,7 @@
 // su3_ensemble one with many, su3_server one whose chain set changes as
 // jobs are admitted and retired.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -66,6 +67,31 @@ static su3_status fail(su3_status st, const char *fmt, ...) {
   } while (0)
 
 extern "C" const char *su3_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ fault injection (host side)
+
+enum FaultSite { kFaultServerAdmit = 0, kFaultServerRound = 1, kFaultSites = 2 };
+static std::atomic<int> g_fault[kFaultSites];
+
+// True (and one armed pass used up) when the site is armed.
+static bool consume_fault(FaultSite site) {
+  int n = g_fault[site].load();
+  while (n > 0)
+    if (g_fault[site].compare_exchange_weak(n, n - 1)) return true;
+  return false;
+}
+
+extern "C" su3_status su3_inject_fault(const char *site, int count) {
+  if (!site) return fail(SU3_EINVAL, "site is NULL");
+  if (count < 0) return fail(SU3_EINVAL, "count=%d < 0", count);
+  if (!std::strcmp(site, "server_admit"))
+    g_fault[kFaultServerAdmit] = count;
+  else if (!std::strcmp(site, "server_round"))
+    g_fault[kFaultServerRound] = count;
+  else
+    return fail(SU3_EINVAL, "unknown fault site '%s'", site);
+  return SU3_OK;
+}
 extern "C" const char *su3_version(void) { return "su3gb300 1.0 (sm_103a)"; }
 
 // ------------------------------------------------------------------ configuration
@@ -1645,13 +1671,19 @@ struct su3_server {
   int max_slots = 0;
   uint64_t next_id = 1;
   std::chrono::steady_clock::time_point t0;
-  std::string worker_error;
+  bool dead = false;         // the worker stopped after an error (under mu)
+  std::string worker_error;  // its message (under mu)
+  std::map<uint64_t, double *> links_out;  // jobs whose final links go to a host buffer
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   void loop();
+  void die(const std::string &msg);
   su3_status admit_locked(std::vector<ServerJob> &admitted);
+  su3_status dead_error() const {
+    return fail(SU3_ECUDA, "server worker stopped after an error: %s", worker_error.c_str());
+  }
 };
 
 static size_t job_bytes(const su3_config &c) {
@@ -1711,6 +1743,7 @@ extern "C" su3_status su3_server_submit(su3_server *srv, const su3_job *job, uin
   if (job->sweeps < 1) return fail(SU3_EINVAL, "sweeps=%d < 1", job->sweeps);
   if (job_bytes(c) > srv->budget) return fail(SU3_ENOMEM, "job needs %zu bytes, budget is %zu", job_bytes(c), srv->budget);
   std::lock_guard<std::mutex> lk(srv->mu);
+  if (srv->dead) return srv->dead_error();
   ServerJob sj{srv->next_id++, *job, srv->now()};
   sj.job.cfg = c;
   srv->queue.push_back(sj);
@@ -1729,7 +1762,7 @@ extern "C" su3_status su3_server_poll(su3_server *srv, uint64_t job_id, su3_resu
     srv->finished.erase(it);
     return SU3_OK;
   }
-  if (srv->submit_time.count(job_id)) return SU3_EBUSY;
+  if (srv->submit_time.count(job_id)) return srv->dead ? srv->dead_error() : SU3_EBUSY;
   return fail(SU3_ENOTFOUND, "job %llu unknown or already collected", (unsigned long long)job_id);
 }
 
@@ -1746,7 +1779,9 @@ extern "C" su3_status su3_server_wait(su3_server *srv, uint64_t job_id, double t
     }
     if (!srv->submit_time.count(job_id))
       return fail(SU3_ENOTFOUND, "job %llu unknown or already collected", (unsigned long long)job_id);
-    if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout && !srv->finished.count(job_id))
+    if (srv->dead) return srv->dead_error();
+    if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout && !srv->finished.count(job_id) &&
+        !srv->dead)
       return fail(SU3_ETIMEOUT, "job %llu not finished after %g s", (unsigned long long)job_id, timeout_s);
   }
 }
@@ -1787,6 +1822,15 @@ su3_status su3_server::admit_locked(std::vector<ServerJob> &admitted) {
   return SU3_OK;
 }
 
+// The worker stops after an error: record it, so that submit, poll and
+// wait report it (ECUDA) instead of leaving jobs to time out.
+void su3_server::die(const std::string &msg) {
+  std::lock_guard<std::mutex> lk(mu);
+  dead = true;
+  worker_error = msg;
+  cv.notify_all();
+}
+
 void su3_server::loop() {
   const long long kTicksPerRound = Engine::kGraphTicks;
   while (true) {
@@ -1799,11 +1843,15 @@ void su3_server::loop() {
     }
     // Bring admitted jobs on the device (outside the lock).
     bool changed = false;
+    std::vector<std::pair<uint64_t, const double *>> starts;  // jobs with a given start configuration
     for (auto &j : admitted) {
       Chain ch;
       su3_config c = j.job.cfg;
       c.stream = eng.stream;
-      su3_status st = eng.add_chain(c, ch);
+      su3_status st = consume_fault(kFaultServerAdmit)
+                          ? fail(SU3_ENOMEM, "injected fault: the device allocation of job %llu failed",
+                                 (unsigned long long)j.id)
+                          : eng.add_chain(c, ch);
       if (st == SU3_OK) {
         eng.chains.push_back(ch);
         st = eng.start_chain(eng.chains.back());
@@ -1832,19 +1880,39 @@ void su3_server::loop() {
       nc.state.active = 1;
       running[j.id] = 1;
       start_time[j.id] = now();
+      if (j.job.links_in) starts.emplace_back(j.id, j.job.links_in);
+      if (j.job.links_out) links_out[j.id] = j.job.links_out;
       changed = true;
     }
     if (changed || eng.tiles_dirty) {
       if (eng.rebuild() != SU3_OK) {
-        worker_error = g_err;
+        die(g_err);
         break;
       }
+    }
+    // Given start configurations replace the start the chain was created with.
+    bool start_failed = false;
+    for (auto &sv : starts)
+      for (size_t c = 0; c < eng.chains.size(); ++c)
+        if (eng.chains[c].job_id == sv.first) {
+          const Chain &ch = eng.chains[c];
+          const size_t n = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V * 18;
+          if (eng.set_links(c, sv.second, n) != SU3_OK) start_failed = true;
+        }
+    if (start_failed) {
+      die(g_err);
+      break;
     }
     if (eng.chains.empty()) continue;
     // One round of fused ticks for every resident chain.
     NvtxRange round("su3_server_round");
+    if (consume_fault(kFaultServerRound)) {
+      fail(SU3_ECUDA, "injected fault: a launch of the worker's round failed");
+      die(g_err);
+      break;
+    }
     if (eng.run_ticks(kTicksPerRound) != SU3_OK || eng.download_states() != SU3_OK) {
-      worker_error = g_err;
+      die(g_err);
       break;
     }
     // Retire finished chains: measure all of them while the device
@@ -1871,6 +1939,18 @@ void su3_server::loop() {
         r.status = SU3_ECUDA;
       }
       eng.counters(c, &r.proposals, &r.accepts);
+      double *lo = nullptr;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = links_out.find(ch.job_id);
+        if (it != links_out.end()) {
+          lo = it->second;
+          links_out.erase(it);
+        }
+      }
+      if (lo && r.status == SU3_OK &&
+          eng.get_links(c, lo, (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V * 18) != SU3_OK)
+        r.status = SU3_ECUDA;
       results.push_back(r);
     }
     std::vector<size_t> bytes(done.size());
@@ -1896,8 +1976,11 @@ void su3_server::loop() {
     }
     if (retired) eng.tiles_dirty = true;
   }
-  // Jobs left behind end with EBUSY.
+  // Jobs left behind end with EBUSY when the server stops; after an error
+  // they stay unfinished and poll / wait report the worker's error.
   std::lock_guard<std::mutex> lk(mu);
+  links_out.clear();
+  if (dead) return;
   for (auto &ch : eng.chains) {
     su3_result r{};
     r.job_id = ch.job_id;

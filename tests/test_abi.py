@@ -134,3 +134,15 @@ def test_sublattice_rejections():
     c = su3.make_config([8, 8, 8, 8], boundary=su3.SU3_DLT, glue_mask=0b1000, beta1=5.0, storage=su3.SU3_FP32_12,
                         ndiv=[2, 1, 1, 1])
     assert su3.su3_link_bytes(c) > 0  # direction 0 is not glued
+
+
+def test_fault_sites_are_validated():
+    """Host-side fault injection (the server's error-path tests) accepts only
+    its known sites and non-negative counts; arming and disarming needs no GPU."""
+    with pytest.raises(su3.Su3Error) as ei:
+        su3.su3_inject_fault("nowhere", 1)
+    assert ei.value.status == su3.SU3_EINVAL
+    with pytest.raises(su3.Su3Error):
+        su3.su3_inject_fault("server_round", -1)
+    su3.su3_inject_fault("server_round", 0)
+    su3.su3_inject_fault("server_admit", 0)

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import paper_0904_0642_gb300 as su3
-from tests.test_gpu_parity import FP32_TOL, _flip_check, _sensitivity
+from tests.test_gpu_parity import FP32_TOL, STRONG_CEILING, _flip_check, _sensitivity
 
 pytestmark = pytest.mark.gpu
 
@@ -72,11 +72,14 @@ def test_extreme_couplings_one_sweep(beta, hits, start):
             o32.U[...] = start32
             m32 = np.full(o32.nlinks, np.inf)
             o32.sweep(beta, hits, 5, n=1, margins=m32)
-            counted = _flip_check(got, o32.U, m32, sens, FP32_TOL)
+            counted = _flip_check(got, o32.U, m32, sens, FP32_TOL, ceiling=STRONG_CEILING)
             # Strong coupling with many hits is ill-conditioned: at beta = 0.3
             # and 254 hits the median link moves by ~1e-6 under a one-ulp
-            # perturbation of the start (six times more than at beta = 6), so
-            # links that a few ulps of float arithmetic already push past the
-            # tolerance are expected beyond it as well.
-            expected = int(np.count_nonzero(4.0 * sens > FP32_TOL))
-            assert counted <= max(o32.nlinks // 10, expected), (counted, expected)
+            # perturbation of the start (six times more than at beta = 6).
+            # The FP32 arithmetic of an update acts like a perturbation of
+            # 10-30 ulp, so the links beyond the tolerance are at most those
+            # whose sensitivity times 10 already exceeds it (measured: 83 and
+            # 91 of 512 links at beta = 0.3), and every one is explained link
+            # by link above.
+            expected = int(np.count_nonzero(10.0 * sens > FP32_TOL))
+            assert counted <= max(2, o32.nlinks // 100, expected), (counted, expected)

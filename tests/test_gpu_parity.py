@@ -20,6 +20,20 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-11
 FP32_TOL = 1e-5
 FLIP_MARGIN = 1e-4  # an FP32 decision this close to the threshold may flip
+# An ill-conditioned link is excused when its error is at most SENS_FACTOR
+# times its sensitivity (its response in the oracle to a one-ulp relative
+# perturbation of the start) and at most an absolute ceiling.  Measured on
+# GB300 over 52 one-sweep cases (every geometry below, both float forms,
+# three seeds each, the two-coupling DLT and the edge couplings; about
+# 40,000 links): the ratio error / sensitivity of every link not near an
+# accept threshold was at most 27.6, the per-case maxima 8-21; the FP32
+# arithmetic of one update acts like a perturbation of 10-30 ulp of the
+# start.  The largest excused error was 1.4e-5 at beta = 6 (ceiling 5e-5)
+# and 9.7e-5 at beta = 0.3 with 254 hits, where the sensitivity itself
+# reaches 4.6e-5 (ceiling 2e-4, STRONG_CEILING).
+SENS_FACTOR = 30.0
+CEILING = 5e-5
+STRONG_CEILING = 2e-4
 
 GEOMS = [
     dict(dims=[4, 4, 4, 4]),
@@ -99,18 +113,20 @@ def _sensitivity(make, start, samples=4, **sweep_kw):
     return out
 
 
-def _flip_check(got, want, margins, sens, tol):
+def _flip_check(got, want, margins, sens, tol, ceiling=CEILING):
     """Links beyond tol are counted, not failed, when the oracle explains
     them: an accept/reject decision within FLIP_MARGIN of its threshold (a
-    flip), or a link whose own response to rounding-level perturbations of
-    the start is large (an ill-conditioned update, e.g. a subgroup with small
-    k, whose direction a/k amplifies the rounding of W); such a link must
-    stay within 30 times that response.  Returns the number counted."""
+    flip: the subgroup's rotation differs entirely, so no bound applies), or
+    a link whose own response to rounding-level perturbations of the start is
+    large (an ill-conditioned update, e.g. a subgroup with small k, whose
+    direction a/k amplifies the rounding of W); such a link must stay within
+    SENS_FACTOR times that response and within the absolute ceiling.
+    Returns the number counted."""
     err = np.max(np.abs(got - want).reshape(-1, 18), axis=1)
     margins = margins.reshape(-1)
     over = err > tol
     flip = margins < FLIP_MARGIN
-    conditioned = err <= np.maximum(tol, 30.0 * sens)
+    conditioned = (err <= SENS_FACTOR * sens) & (err <= ceiling)
     unexplained = over & ~flip & ~conditioned
     assert not unexplained.any(), (
         f"{int(unexplained.sum())} links differ beyond the FP32 bound: err={err[unexplained][:5]}, "
@@ -212,9 +228,9 @@ def test_reunitarize_matches_oracle(storage, tol):
 @pytest.mark.parametrize("glue", [0b1111, 0b1000])
 def test_two_couplings_one_sweep(glue):
     """DLT with beta0 != beta1 (Sec. 2.2): FP64 link by link against the
-    oracle; FP32 within 2e-5 - the beta-weighted staple sums terms of size
-    beta_p, so its float rounding is relatively larger than for one beta
-    (worst measured 1.01e-5 on 1024 links)."""
+    oracle; FP32 within the FP32 tolerance, every link beyond it explained by
+    the oracle as in test_one_sweep_fp32 (the beta-weighted staple sums terms
+    of size beta_p, so a few ill-conditioned links land just above 1e-5)."""
     g = dict(dims=[4, 2, 4, 4], nlayers=2, glue_mask=glue)
     o = oracle_lattice(g).hot_start(19)
     start = o.U.copy()
@@ -232,5 +248,5 @@ def test_two_couplings_one_sweep(glue):
         o2.sweep(6.0, 2, 5, n=1, beta1=4.2, margins=margins)
         sens = _sensitivity(lambda: oracle_lattice(g), start32, beta=6.0, hits=2, seed=5, n=1, beta1=4.2)
         lat.sweep(1)
-        counted = _flip_check(lat.get_links(), o2.U, margins, sens, 2 * FP32_TOL)
+        counted = _flip_check(lat.get_links(), o2.U, margins, sens, FP32_TOL)
     assert counted <= max(2, o2.nlinks // 100)
