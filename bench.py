@@ -210,11 +210,42 @@ def cpu_baseline():
     return out
 
 
+def graph_stage_times(su3, torch, stream, seed, step_ms):
+    """Per-stage device times of the 32^4 step, all from CUDA-graph-timed
+    runs (CUDA events on the lattice's stream), so that they add up to the
+    timed step: a lattice re-unitarised every 10 sweeps runs 80 update ticks
+    + 1 re-unitarisation per 10-sweep call (T10), one re-unitarised every 20
+    sweeps 160 + 1 per 20-sweep call (T20); neither measures.  Then
+    update tick = (T20 - T10) / 80, re-unitarisation = T10 - 80 x tick (it
+    carries the call's one-block arm kernel), measurement = step - T10."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per_call = {}
+    for every, calls in ((10, 12), (20, 6)):
+        lat = su3.Lattice(DIMS, beta=BETA, seed=seed, hits=HITS, storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT,
+                          reunit_every=every, stream=stream)
+        lat.autotune()
+        lat.sweep(every)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(calls):
+            lat.sweep(every)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_call[every] = e0.elapsed_time(e1) / calls
+        lat.close()
+    ticks = 2 * len(DIMS) * SWEEPS_PER_STEP
+    tick_ms = (per_call[20] - per_call[10]) / ticks
+    reunit_ms = per_call[10] - ticks * tick_ms
+    return {"update_tick_us": 1e3 * tick_ms, "reunit_us": 1e3 * reunit_ms,
+            "measure_us": 1e3 * (step_ms - per_call[10]), "T10_ms": per_call[10], "T20_ms": per_call[20],
+            "sum_ms": ticks * tick_ms + reunit_ms + (step_ms - per_call[10]), "step_ms": step_ms}
+
+
 # ---------------------------------------------------------------- other workloads
 # Each is reported as an extra key of the bench line (same JSON line).
 
 
-def bench_ensemble(su3, torch, stream):
+def bench_ensemble(su3, torch, stream, peaks):
     """256 independent 8^4 chains, beta_c ~ U[5.5, 6.5], FP32, one fused
     persistent launch per phase, graph-captured, autotuned; against the same
     chains swept one after another as single-chain lattices."""
@@ -235,6 +266,17 @@ def bench_ensemble(su3, torch, stream):
     torch.cuda.synchronize()
     t_ens = e0.elapsed_time(e1) * 1e-3
     links = 256 * 8 ** 4 * 4
+    # the update ticks' share of the graph-timed run: the run's re-unitarisation
+    # ticks (every 10 sweeps) are timed with per-tick events and taken out
+    ens.set_profiling(True)
+    ens.profile(reset=True)
+    ens.sweep(10)
+    prof = ens.profile(reset=True)
+    ens.set_profiling(False)
+    reunit_ms = prof["reunit_ms"] / max(1, prof["reunit_launches"])
+    n_upd = sweeps * 2 * 4
+    tick_s = (1e3 * t_ens - (sweeps // 10) * reunit_ms) / n_upd * 1e-3
+    alg = 256 * (8 ** 4 // 2) * (2 * 4 + 1) * 48
     # 256 sequential single-chain runs (fewer sweeps each, same per-sweep work)
     seq_sweeps = 20
     lats = [su3.Lattice([8, 8, 8, 8], beta=float(b), seed=5000 + c, storage=su3.SU3_FP32_12,
@@ -258,6 +300,10 @@ def bench_ensemble(su3, torch, stream):
     return {"workload": "256 chains of 8^4 PBC, beta ~ U[5.5,6.5], FP32, 200 sweeps, fused + graph",
             "value": fused, "unit": UNIT, "sequential_single_chain": seq, "speedup": fused / seq,
             "launch": {"variant": var, "threads": thr, "ctas_per_sm": ctas},
+            "update_tick_us": tick_s * 1e6, "alg_bytes_per_update_tick": alg,
+            "achieved_gbs": alg / tick_s / 1e9, "hbm_frac": alg / tick_s / 1e9 / peaks["hbm_gbs"],
+            "tick_source": "graph-timed 200 sweeps minus 20 event-timed re-unitarisation ticks, over 1600 "
+                           "update ticks (524288 link updates x (2D+1) x 48 B each)",
             "plaquette_mean": float(meas[:, 0].mean())}
 
 
@@ -344,25 +390,38 @@ def bench_dlt_and_d3(su3, torch, stream):
     return out
 
 
-def bench_serving(su3, torch, n_jobs=60, n_fp64=8):
-    """Poisson arrivals (50 jobs/s) of mixed jobs into the continuous-batching
-    server; p50/p99 latency and throughput, against a plain FP64
-    one-job-at-a-time loop over the first n_fp64 jobs (its latencies come
-    from the same arrival times with FIFO service)."""
+SERVE_SHAPES = [[8, 8, 8, 8], [12, 12, 12, 12], [16, 16, 16, 4], [24, 24, 24, 24], [32, 32, 32, 8], [48, 48, 48]]
+
+
+def serving_jobs(su3, n, rate, seed):
+    """n jobs with Poisson arrivals at `rate` per second: shape uniform over
+    the six serving shapes, DLT with probability 0.2, beta ~ U[5.6, 6.4],
+    sweeps ~ U{50..500}; (arrival s, dims, boundary, beta, sweeps, seed)."""
     import numpy as np
-    rng = np.random.default_rng(50)
-    shapes = [[8, 8, 8, 8], [12, 12, 12, 12], [16, 16, 16, 4], [24, 24, 24, 24], [32, 32, 32, 8], [48, 48, 48]]
-    jobs = []
-    t = 0.0
-    for j in range(n_jobs):
-        t += rng.exponential(1 / 50.0)
-        dims = shapes[rng.integers(len(shapes))]
+    rng = np.random.default_rng(seed)
+    jobs, t = [], 0.0
+    for j in range(n):
+        t += rng.exponential(1 / rate)
+        dims = SERVE_SHAPES[rng.integers(len(SERVE_SHAPES))]
         boundary = su3.SU3_DLT if rng.random() < 0.2 else su3.SU3_PBC
         jobs.append((t, dims, boundary, float(rng.uniform(5.6, 6.4)), int(rng.integers(50, 501)), 7000 + j))
+    return jobs
 
-    def links_of(dims, boundary):
-        return int(np.prod(dims)) * len(dims) * (2 if boundary == su3.SU3_DLT else 1)
 
+def _links(su3, dims, boundary):
+    n = len(dims) * (2 if boundary == su3.SU3_DLT else 1)
+    for d in dims:
+        n *= d
+    return n
+
+
+def serve_fp32(su3, jobs, peaks, window=(0.0, 1.0)):
+    """The jobs through the continuous-batching server as they arrive.
+    Latency = completion - submission (host clock).  p50 / p99 over the jobs
+    whose arrival rank lies in `window` (a steady-state window excludes the
+    ramp-up and ramp-down); throughput over the whole run; the HBM fraction
+    over the device time of the server's rounds."""
+    import numpy as np
     srv = su3.Server(max_slots=64)
     t0 = time.perf_counter()
     ids = []
@@ -372,38 +431,83 @@ def bench_serving(su3, torch, n_jobs=60, n_fp64=8):
             time.sleep(ta - now)
         cfg = su3.make_config(dims, boundary=b, beta=beta, seed=seed, storage=su3.SU3_FP32_12,
                               start=su3.SU3_START_HOT, hits=HITS, reunit_every=10)
-        ids.append((srv.submit(cfg, sw), time.perf_counter() - t0))
-    lat_s = []
-    for (jid, tsub), (ta, dims, b, beta, sw, seed) in zip(ids, jobs):
-        r = srv.wait(jid, timeout_s=600)
-        lat_s.append(r.finish_s - r.submit_s)
+        ids.append(srv.submit(cfg, sw))
+    res = [srv.wait(j, timeout_s=900) for j in ids]
     t_all = time.perf_counter() - t0
+    rounds, dev_ms = srv.stats()
     srv.close()
-    total_updates = sum(links_of(d, b) * sw for (_, d, b, _, sw, _) in jobs)
-    # plain FP64 one job at a time, FIFO over the same arrival times
-    service = []
-    for (ta, dims, b, beta, sw, seed) in jobs[:n_fp64]:
+    lat_s = np.array([r.finish_s - r.submit_s for r in res])
+    lo, hi = int(window[0] * len(jobs)), int(window[1] * len(jobs))
+    upd = sum(_links(su3, d, b) * sw for (_, d, b, _, sw, _) in jobs)
+    alg = sum(_links(su3, d, b) * sw * (2 * len(d) + 1) * 48 for (_, d, b, _, sw, _) in jobs)
+    return {"jobs": len(jobs), "offered_jobs_per_s": len(jobs) / jobs[-1][0], "jobs_per_s": len(jobs) / t_all,
+            "link_updates_per_s": upd / t_all, "latency_p50_s": float(np.percentile(lat_s[lo:hi], 50)),
+            "latency_p99_s": float(np.percentile(lat_s[lo:hi], 99)), "latency_jobs": hi - lo,
+            "rounds": rounds, "device_s": dev_ms * 1e-3, "achieved_gbs": alg / (dev_ms * 1e-3) / 1e9,
+            "hbm_frac": alg / (dev_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "statuses_ok": all(r.status == su3.SU3_OK for r in res),
+            "plaquettes": [float(r.plaquette[0]) for r in res]}
+
+
+def serve_fp64_one_at_a_time(su3, torch, jobs):
+    """The plain FP64 baseline under the same arrivals: one FP64 18-real
+    single-chain lattice at a time, in arrival order; a job waits for the
+    previous one.  Latency = completion - arrival, measured."""
+    import numpy as np
+    t0 = time.perf_counter()
+    lat_s, plaq, busy = [], [], 0.0
+    for (ta, dims, b, beta, sw, seed) in jobs:
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        s0 = time.perf_counter()
         lat = su3.Lattice(dims, boundary=b, beta=beta, seed=seed, storage=su3.SU3_FP64_18, start=su3.SU3_START_HOT,
                           hits=HITS, reunit_every=10)
-        torch.cuda.synchronize()
-        s0 = time.perf_counter()
         lat.sweep(sw)
-        lat.plaquette()
-        service.append(time.perf_counter() - s0)
+        plaq.append(lat.plaquette()[0])  # synchronises
         lat.close()
-    free_at, lat64 = 0.0, []
-    for (ta, *_), sv in zip(jobs[:n_fp64], service):
-        start = max(ta, free_at)
-        free_at = start + sv
-        lat64.append(free_at - ta)
-    return {"workload": f"{n_jobs} Poisson jobs (50/s), shapes 8^4..48^3, 20% DLT, 50-500 sweeps, FP32 + FP64 "
-                        "reunitarize/reductions",
-            "jobs_per_s": n_jobs / t_all, "link_updates_per_s": total_updates / t_all,
-            "latency_p50_s": float(np.percentile(lat_s, 50)), "latency_p99_s": float(np.percentile(lat_s, 99)),
-            "fp64_one_at_a_time": {"jobs": n_fp64, "latency_p50_s": float(np.percentile(lat64, 50)),
-                                   "latency_p99_s": float(np.percentile(lat64, 99)),
-                                   "link_updates_per_s": sum(links_of(d, b) * sw for (_, d, b, _, sw, _) in
-                                                             jobs[:n_fp64]) / sum(service)}}
+        done = time.perf_counter()
+        busy += done - s0
+        lat_s.append(done - t0 - ta)
+    upd = sum(_links(su3, d, b) * sw for (_, d, b, _, sw, _) in jobs)
+    return {"jobs": len(jobs), "latency_p50_s": float(np.percentile(lat_s, 50)),
+            "latency_p99_s": float(np.percentile(lat_s, 99)), "link_updates_per_s_busy": upd / busy,
+            "plaquettes": plaq}
+
+
+def bench_serving(su3, torch, peaks):
+    """BASELINE config 5: Poisson arrivals of mixed jobs into the
+    continuous-batching server (FP32 12-real links, FP64 re-unitarisation
+    and reductions), against a plain FP64 one-job-at-a-time loop under the
+    same arrivals."""
+    import numpy as np
+    out = {"workload": "Poisson jobs, shapes 8^4/12^4/16^3x4/24^4/32^3x8/48^3, 20% DLT, beta U[5.6,6.4], "
+                       "50-500 sweeps, FP32 + FP64 reunitarize/reductions"}
+    # the same 50 jobs at 50/s: served in FP32, and one at a time in FP64
+    jobs50 = serving_jobs(su3, 50, 50.0, 50)
+    a = serve_fp32(su3, jobs50, peaks)
+    b = serve_fp64_one_at_a_time(su3, torch, jobs50)
+    d = np.array(a.pop("plaquettes")) - np.array(b.pop("plaquettes"))
+    out["fp32_50_jobs_at_50_per_s"] = a
+    out["fp64_one_at_a_time_50_jobs_at_50_per_s"] = b
+    # observable accuracy: the FP32 and FP64 chains of a job start alike but
+    # decorrelate over tens of sweeps, so their final plaquettes are two
+    # samples of the same distribution; their mean difference over the jobs
+    # must be consistent with zero
+    out["plaquette_fp32_minus_fp64"] = {"mean": float(d.mean()), "stderr": float(d.std(ddof=1) / np.sqrt(len(d))),
+                                        "max_abs": float(np.abs(d).max())}
+    # 500 jobs at 50/s: above the server's capacity (the queue grows; the
+    # latencies include the growing wait)
+    c = serve_fp32(su3, serving_jobs(su3, 500, 50.0, 51), peaks)
+    c.pop("plaquettes")
+    c["note"] = "offered load above capacity: no steady state, latencies include the growing queue"
+    out["fp32_500_jobs_at_50_per_s"] = c
+    # 500 jobs at 25/s: sustainable; latencies over the steady-state window
+    # (arrival ranks 10 %..90 %)
+    e = serve_fp32(su3, serving_jobs(su3, 500, 25.0, 52), peaks, window=(0.1, 0.9))
+    e.pop("plaquettes")
+    out["fp32_500_jobs_at_25_per_s"] = e
+    return out
 
 
 def main():
@@ -484,14 +588,20 @@ def main():
     line["clocks"] = clocks
 
     if not args.no_extras:
-        # Roofline: live per-kernel CUDA-event timing of the update-phase launches.
+        # Roofline of the dominant kernel, the update tick.  Its duration comes
+        # from graph-timed runs (CUDA events on the launching stream, the
+        # launch overlap of the timed step included), so that 80 ticks + the
+        # re-unitarisation + the measurement add up to ms_per_step; the
+        # per-tick event timing (each tick wrapped in its own events, which
+        # loses the overlap of consecutive launches) is reported beside it.
         peaks, peak_src = measured_peaks()
+        st = graph_stage_times(su3, torch, stream, reps.seed(SEED), ms_max / args.steps)
         lat.set_profiling(True)
         lat.profile(reset=True)
         lat.sweep(SWEEPS_PER_STEP)
         prof = lat.profile(reset=True)
         lat.set_profiling(False)
-        upd_ms = prof["update_ms"] / max(1, prof["update_launches"])
+        upd_ms = st["update_tick_us"] * 1e-3
         V = links // len(DIMS)
         alg_bytes = (V // 2) * (2 * len(DIMS) + 1) * 48
         achieved = alg_bytes / (upd_ms * 1e-3) / 1e9
@@ -499,8 +609,14 @@ def main():
                             "frac": achieved / peaks["hbm_gbs"], "traffic": recorded_traffic("k_tick_fp32_update"),
                             "peak_source": f"hbm_gbs of {peak_src}", "kernel": "k_tick<StoreF32x12> update phase",
                             "alg_bytes_per_launch": alg_bytes, "avg_launch_us": upd_ms * 1e3,
-                            "reunit_us": 1e3 * prof["reunit_ms"] / max(1, prof["reunit_launches"]),
-                            "measure_us": 1e3 * prof["measure_ms"] / max(1, prof["measure_launches"])}
+                            "tick_source": "graph-timed: (T(20 sweeps, re-unitarised every 20) - T(10 sweeps, "
+                                           "every 10)) / 80 update ticks",
+                            "reunit_us": st["reunit_us"], "measure_us": st["measure_us"],
+                            "stages_sum_ms": st["sum_ms"], "step_ms": st["step_ms"],
+                            "event_timed_us": {
+                                "update": 1e3 * prof["update_ms"] / max(1, prof["update_launches"]),
+                                "reunit": 1e3 * prof["reunit_ms"] / max(1, prof["reunit_launches"]),
+                                "measure": 1e3 * prof["measure_ms"] / max(1, prof["measure_launches"])}}
 
         # End to end through the C ABI: every step uploads that step's input
         # configuration from pinned host memory (su3_stage_links_ex on the
@@ -588,11 +704,11 @@ def main():
         ref32.close()
         lat64.close()
         if rank == 0 and world == 1:
-            line["ensemble_256x8^4"] = bench_ensemble(su3, torch, stream)
+            line["ensemble_256x8^4"] = bench_ensemble(su3, torch, stream, peaks)
             line["fp32_18_32^4"] = bench_fp32_18(su3, torch, stream, peaks)
             line["divided_32^4_2x2x2x2"] = bench_divided(su3, torch, stream)
             line.update(bench_dlt_and_d3(su3, torch, stream))
-            line["serving"] = bench_serving(su3, torch)
+            line["serving"] = bench_serving(su3, torch, peaks)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -416,6 +416,10 @@ su3_status su3_server_poll(su3_server *srv, uint64_t job_id, su3_result *out);
 su3_status su3_server_wait(su3_server *srv, uint64_t job_id, double timeout_s, su3_result *out);
 /* Jobs queued, resident, and finished-but-uncollected. */
 su3_status su3_server_load(su3_server *srv, int *queued, int *resident, int *finished);
+/* Rounds of fused ticks the worker has run and their device time in
+ * milliseconds (CUDA events around each round on the worker's stream: the
+ * kernels of the rounds, without the host work between rounds). */
+su3_status su3_server_stats(su3_server *srv, uint64_t *rounds, double *device_ms);
 /* Stops the scheduler; jobs still queued or running end with SU3_EBUSY. */
 void su3_server_destroy(su3_server *srv);
 

@@ -40,7 +40,8 @@ EXPORTED = [
     "su3_ensemble_measure", "su3_ensemble_get_links", "su3_ensemble_measurements", "su3_ensemble_set_launch", "su3_ensemble_autotune", "su3_ensemble_use_graph",
     "su3_ensemble_set_profiling", "su3_ensemble_get_profile",
     "su3_server_create", "su3_server_submit", "su3_server_poll", "su3_server_wait", "su3_server_load",
-    "su3_server_destroy", "su3_last_error", "su3_version", "su3_measure_noalloc", "su3_inject_fault",
+    "su3_server_destroy", "su3_server_stats", "su3_last_error", "su3_version", "su3_measure_noalloc",
+    "su3_inject_fault",
 ]
 
 
@@ -146,6 +147,7 @@ def lib():
             "su3_version": (c_char_p, []),
             "su3_measure_noalloc": (c_int, [POINTER(su3_config), vp, vp, vp]),
             "su3_inject_fault": (c_int, [c_char_p, c_int]),
+            "su3_server_stats": (c_int, [vp, u64p, dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -675,3 +677,9 @@ class Server:
         q, r, f = c_int(), c_int(), c_int()
         _check(lib().su3_server_load(self.h, byref(q), byref(r), byref(f)))
         return q.value, r.value, f.value
+
+    def stats(self):
+        """(rounds run, their device time in ms)."""
+        n, ms = c_uint64(), c_double()
+        _check(lib().su3_server_stats(self.h, byref(n), byref(ms)))
+        return n.value, ms.value

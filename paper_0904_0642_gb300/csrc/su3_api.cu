@@ -1671,6 +1671,9 @@ struct su3_server {
   int max_slots = 0;
   uint64_t next_id = 1;
   std::chrono::steady_clock::time_point t0;
+  cudaEvent_t round_ev[2] = {nullptr, nullptr};  // around each round of ticks
+  uint64_t rounds = 0;       // rounds run (under mu)
+  double device_ms = 0.0;    // their device time (under mu)
   bool dead = false;         // the worker stopped after an error (under mu)
   std::string worker_error;  // its message (under mu)
   std::map<uint64_t, double *> links_out;  // jobs whose final links go to a host buffer
@@ -1724,6 +1727,12 @@ extern "C" su3_status su3_server_create(size_t hbm_budget_bytes, int max_slots, 
     int occ = 0;
     if (tick_occupancy(SU3_FP32_12, srv->eng.variant, false, false, srv->eng.block, &occ) != cudaSuccess || occ < 1) occ = 1;
     srv->eng.ctas_per_sm = occ;
+  }
+  if (cudaEventCreate(&srv->round_ev[0]) != cudaSuccess || cudaEventCreate(&srv->round_ev[1]) != cudaSuccess) {
+    srv->eng.release();
+    cudaStreamDestroy(st);
+    delete srv;
+    return fail(SU3_ECUDA, "cudaEventCreate failed");
   }
   srv->t0 = std::chrono::steady_clock::now();
   srv->worker = std::thread([srv] { srv->loop(); });
@@ -1795,6 +1804,14 @@ extern "C" su3_status su3_server_load(su3_server *srv, int *queued, int *residen
   return SU3_OK;
 }
 
+extern "C" su3_status su3_server_stats(su3_server *srv, uint64_t *rounds, double *device_ms) {
+  if (!srv) return fail(SU3_EINVAL, "server handle is NULL");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (rounds) *rounds = srv->rounds;
+  if (device_ms) *device_ms = srv->device_ms;
+  return SU3_OK;
+}
+
 extern "C" void su3_server_destroy(su3_server *srv) {
   if (!srv) return;
   {
@@ -1805,6 +1822,8 @@ extern "C" void su3_server_destroy(su3_server *srv) {
   if (srv->worker.joinable()) srv->worker.join();
   cudaStream_t st = srv->eng.stream;
   srv->eng.release();
+  for (cudaEvent_t e : srv->round_ev)
+    if (e) cudaEventDestroy(e);
   if (st) cudaStreamDestroy(st);
   delete srv;
 }
@@ -1911,9 +1930,21 @@ void su3_server::loop() {
       die(g_err);
       break;
     }
-    if (eng.run_ticks(kTicksPerRound) != SU3_OK || eng.download_states() != SU3_OK) {
+    cudaError_t ev = cudaEventRecord(round_ev[0], eng.stream);
+    su3_status rs = ev == cudaSuccess ? eng.run_ticks(kTicksPerRound) : SU3_ECUDA;
+    if (rs == SU3_OK) ev = cudaEventRecord(round_ev[1], eng.stream);
+    if (rs == SU3_OK && ev == cudaSuccess) rs = eng.download_states();
+    if (ev != cudaSuccess) rs = fail(SU3_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(ev));
+    if (rs != SU3_OK) {
       die(g_err);
       break;
+    }
+    {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, round_ev[0], round_ev[1]);  // both complete: download_states synchronised
+      std::lock_guard<std::mutex> lk(mu);
+      rounds += 1;
+      device_ms += ms;
     }
     // Retire finished chains: measure all of them while the device
     // descriptors still match the host order, then release in reverse.
