@@ -180,7 +180,9 @@ su3_status su3_measurement_latest(su3_lattice *lat, double *host_out, size_t n);
  * pipelined caller reads step k's result while step k+1 runs. */
 su3_status su3_measurement_latest_async(su3_lattice *lat, double *host_out, size_t n);
 
-/* Wait until all work queued on the lattice's stream has finished. */
+/* Wait until all work queued on the lattice's stream has finished.  In a
+ * debug-bounds build also SU3_ECUDA when a device bounds check has failed
+ * (see su3_bounds_status). */
 su3_status su3_synchronize(su3_lattice *lat);
 
 /* The same with a deadline (a host-side watchdog): polls an event recorded
@@ -434,6 +436,24 @@ void su3_server_destroy(su3_server *srv);
  *                   launch would (the worker stops; see su3_server_poll).
  * EINVAL for an unknown site or a negative count. */
 su3_status su3_inject_fault(const char *site, int count);
+
+/* ---------------------------------------------------------------- debug bounds checks
+ * A library built with SU3_DEBUG_BOUNDS (libsu3gb300_dbg.so, built beside
+ * the release library) checks every link access and every scratch index on
+ * the device against its extent before the access.  The first violation is
+ * recorded in device memory and the access is skipped; nothing traps, so
+ * the context stays usable.  su3_synchronize then returns SU3_ECUDA with the
+ * violation in su3_last_error.  The release library compiles the checks
+ * out: there su3_bounds_status always reports none.
+ *
+ * su3_bounds_status: the first recorded violation (site code, index,
+ *   extent; site 0: none); SU3_OK when none, SU3_ECUDA otherwise.  The
+ *   record is sticky for the life of the process.  Synchronises the device.
+ * su3_bounds_selftest: records a deliberate violation (an index equal to
+ *   its extent, checked but never used for an access) to test the reporting
+ *   path; SU3_EINVAL in the release library. */
+su3_status su3_bounds_status(uint64_t *site, int64_t *index, int64_t *extent);
+su3_status su3_bounds_selftest(void);
 
 /* Thread-local message of the last error (empty string if none). */
 const char *su3_last_error(void);

@@ -23,7 +23,9 @@ from ctypes import (POINTER, Structure, byref, c_char_p, c_double, c_int, c_int3
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsu3gb300.so")
+# SU3_DEBUG_BOUNDS=1 selects the build with device bounds checks (see
+# su3_bounds_status in include/su3.h)
+LIB_PATH = os.path.join(_HERE, "libsu3gb300_dbg.so" if os.environ.get("SU3_DEBUG_BOUNDS") == "1" else "libsu3gb300.so")
 MAX_D = 4
 
 SU3_OK, SU3_EINVAL, SU3_ENOMEM, SU3_ECUDA, SU3_ETIMEOUT, SU3_EBUSY, SU3_ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
@@ -41,7 +43,7 @@ EXPORTED = [
     "su3_ensemble_set_profiling", "su3_ensemble_get_profile",
     "su3_server_create", "su3_server_submit", "su3_server_poll", "su3_server_wait", "su3_server_load",
     "su3_server_destroy", "su3_server_stats", "su3_last_error", "su3_version", "su3_measure_noalloc",
-    "su3_inject_fault",
+    "su3_inject_fault", "su3_bounds_status", "su3_bounds_selftest",
 ]
 
 
@@ -148,6 +150,8 @@ def lib():
             "su3_measure_noalloc": (c_int, [POINTER(su3_config), vp, vp, vp]),
             "su3_inject_fault": (c_int, [c_char_p, c_int]),
             "su3_server_stats": (c_int, [vp, u64p, dp]),
+            "su3_bounds_status": (c_int, [u64p, POINTER(c_int64), POINTER(c_int64)]),
+            "su3_bounds_selftest": (c_int, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -338,6 +342,22 @@ def su3_get_profile(h, reset: bool = False) -> dict:
     p = su3_profile()
     _check(lib().su3_get_profile(h, byref(p), int(bool(reset))))
     return {k: getattr(p, k) for k, _ in su3_profile._fields_}
+
+
+def su3_bounds_status():
+    """(site, index, extent) of the first device bounds violation recorded by
+    a debug-bounds build, site 0 when none; raises Su3Error (SU3_ECUDA)
+    when one was recorded."""
+    site, idx, ext = c_uint64(), c_int64(), c_int64()
+    st = lib().su3_bounds_status(byref(site), byref(idx), byref(ext))
+    rec = (site.value, idx.value, ext.value)
+    if st != SU3_OK:
+        raise Su3Error(st, lib().su3_last_error().decode() + f" {rec}")
+    return rec
+
+
+def su3_bounds_selftest():
+    _check(lib().su3_bounds_selftest())
 
 
 def su3_inject_fault(site: str, count: int = 1):

@@ -92,7 +92,50 @@ extern "C" su3_status su3_inject_fault(const char *site, int count) {
     return fail(SU3_EINVAL, "unknown fault site '%s'", site);
   return SU3_OK;
 }
-extern "C" const char *su3_version(void) { return "su3gb300 1.0 (sm_103a)"; }
+extern "C" const char *su3_version(void) {
+  return debug_bounds_build() ? "su3gb300 1.0 (sm_103a, debug bounds)" : "su3gb300 1.0 (sm_103a)";
+}
+
+// ------------------------------------------------------------------ debug bounds checks
+
+static const char *bounds_site_name(unsigned long long site) {
+  switch (site) {
+    case 1: return "link plane (layer, colour, direction)";
+    case 2: return "checkerboard index";
+    case 3: return "link plane offset";
+    case 4: return "measurement partial-sum slot";
+    case 5: return "action bookkeeping slot";
+    case 9: return "self-test";
+    default: return "unknown site";
+  }
+}
+
+// ECUDA with the first recorded device bounds violation (debug-bounds
+// builds; always OK otherwise).
+static su3_status bounds_status() {
+  if (!debug_bounds_build()) return SU3_OK;
+  unsigned long long r[3];
+  CU(bounds_record(r));
+  if (r[0])
+    return fail(SU3_ECUDA, "device bounds check: %s %lld outside [0, %lld)", bounds_site_name(r[0]), (long long)r[1],
+                (long long)r[2]);
+  return SU3_OK;
+}
+
+extern "C" su3_status su3_bounds_status(uint64_t *site, int64_t *index, int64_t *extent) {
+  unsigned long long r[3] = {0, 0, 0};
+  if (debug_bounds_build()) CU(bounds_record(r));
+  if (site) *site = r[0];
+  if (index) *index = (int64_t)r[1];
+  if (extent) *extent = (int64_t)r[2];
+  return bounds_status();
+}
+
+extern "C" su3_status su3_bounds_selftest(void) {
+  if (!debug_bounds_build()) return fail(SU3_EINVAL, "not a debug-bounds build (SU3_DEBUG_BOUNDS)");
+  CU(launch_bounds_selftest());
+  return SU3_OK;
+}
 
 // ------------------------------------------------------------------ configuration
 
@@ -1258,7 +1301,7 @@ extern "C" su3_status su3_measurement_latest_async(su3_lattice *lat, double *hos
 extern "C" su3_status su3_synchronize(su3_lattice *lat) {
   LAT_CHECK(lat);
   CU(cudaStreamSynchronize(lat->eng.stream));
-  return SU3_OK;
+  return bounds_status();
 }
 
 extern "C" su3_status su3_wait(su3_lattice *lat, double timeout_s) {

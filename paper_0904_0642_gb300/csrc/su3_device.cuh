@@ -9,6 +9,41 @@
 
 namespace su3g {
 
+// ------------------------------------------------------------------ debug bounds checks
+// Built with SU3_DEBUG_BOUNDS, every link access and every scratch index is
+// checked against its extent before the access.  The first violation is
+// recorded in g_bounds (site code, index, extent) and the access is skipped
+// (a load gives zeros); nothing traps, so the context stays usable and the
+// host reports the violation (su3_bounds_status, su3_synchronize).  Without
+// the flag the checks compile to nothing.
+#ifdef SU3_DEBUG_BOUNDS
+static __device__ unsigned long long g_bounds[3];
+#endif
+enum BoundsSite : unsigned {
+  kBoundsPlane = 1,    // (layer, colour, direction) of a link plane
+  kBoundsIndex = 2,    // checkerboard index within a plane
+  kBoundsLink = 3,     // plane offset of a precomputed link index
+  kBoundsPartial = 4,  // measurement partial-sum slot
+  kBoundsSlot = 5,     // action bookkeeping slot
+  kBoundsSelfTest = 9  // the self-test's deliberate out-of-range index (never accessed)
+};
+
+__device__ __forceinline__ bool in_bounds(long long i, long long n, unsigned site) {
+#ifdef SU3_DEBUG_BOUNDS
+  if (i >= 0 && i < n) return true;
+  if (atomicCAS(&g_bounds[0], 0ull, (unsigned long long)site) == 0ull) {
+    g_bounds[1] = (unsigned long long)i;
+    g_bounds[2] = (unsigned long long)n;
+  }
+  return false;
+#else
+  (void)i;
+  (void)n;
+  (void)site;
+  return true;
+#endif
+}
+
 // ------------------------------------------------------------------ complex 3x3
 
 template <typename R>
@@ -348,6 +383,7 @@ struct StoreF32x12 {
   static constexpr bool kTwoRows = true;
   // rows 0, 1 only (row 2 left unset)
   __device__ static __forceinline__ M3<float> load2(const Vec *plane, int Vh, int jj) {
+    if (!in_bounds(jj, Vh, kBoundsIndex)) return m3_zero<float>();
     const Vec *p = plane + jj;
     const float4 q0 = __ldg(p), q1 = __ldg(p + Vh), q2 = __ldg(p + 2 * Vh);
     M3<float> m;
@@ -365,12 +401,14 @@ struct StoreF32x12 {
     return m;
   }
   __device__ static __forceinline__ void store(Vec *plane, int Vh, int jj, const M3<float> &m) {
+    if (!in_bounds(jj, Vh, kBoundsIndex)) return;
     Vec *p = plane + jj;
     p[0] = make_float4(m.e[0][0].re, m.e[0][0].im, m.e[0][1].re, m.e[0][1].im);
     p[Vh] = make_float4(m.e[0][2].re, m.e[0][2].im, m.e[1][0].re, m.e[1][0].im);
     p[2 * Vh] = make_float4(m.e[1][1].re, m.e[1][1].im, m.e[1][2].re, m.e[1][2].im);
   }
   __device__ static __forceinline__ void copy(Vec *dst, int dVh, int dj, const Vec *src, int sVh, int sj) {
+    if (!(in_bounds(dj, dVh, kBoundsIndex) && in_bounds(sj, sVh, kBoundsIndex))) return;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) dst[(size_t)q * dVh + dj] = src[(size_t)q * sVh + sj];
   }
@@ -389,6 +427,7 @@ struct StoreF32x18 {
   static constexpr int NQ = 9;  // float2 units per link
   static constexpr bool kTwoRows = false;
   __device__ static __forceinline__ M3<float> load2(const Vec *plane, int Vh, int jj) {
+    if (!in_bounds(jj, Vh, kBoundsIndex)) return m3_zero<float>();
     const float4 *p = reinterpret_cast<const float4 *>(plane) + jj;
     const float4 q0 = __ldg(p), q1 = __ldg(p + Vh), q2 = __ldg(p + 2 * Vh);
     M3<float> m;
@@ -402,6 +441,7 @@ struct StoreF32x18 {
   }
   __device__ static __forceinline__ M3<float> load(const Vec *plane, int Vh, int jj) {
     M3<float> m = load2(plane, Vh, jj);
+    if (!in_bounds(jj, Vh, kBoundsIndex)) return m;
     const float4 q3 = __ldg(reinterpret_cast<const float4 *>(plane) + 3 * Vh + jj);
     const float2 q4 = __ldg(plane + 8 * Vh + jj);
     m.e[2][0] = {q3.x, q3.y};
@@ -410,6 +450,7 @@ struct StoreF32x18 {
     return m;
   }
   __device__ static __forceinline__ void store(Vec *plane, int Vh, int jj, const M3<float> &m) {
+    if (!in_bounds(jj, Vh, kBoundsIndex)) return;
     float4 *p = reinterpret_cast<float4 *>(plane) + jj;
     p[0] = make_float4(m.e[0][0].re, m.e[0][0].im, m.e[0][1].re, m.e[0][1].im);
     p[Vh] = make_float4(m.e[0][2].re, m.e[0][2].im, m.e[1][0].re, m.e[1][0].im);
@@ -418,6 +459,7 @@ struct StoreF32x18 {
     plane[8 * Vh + jj] = make_float2(m.e[2][2].re, m.e[2][2].im);
   }
   __device__ static __forceinline__ void copy(Vec *dst, int dVh, int dj, const Vec *src, int sVh, int sj) {
+    if (!(in_bounds(dj, dVh, kBoundsIndex) && in_bounds(sj, sVh, kBoundsIndex))) return;
     float4 *d4 = reinterpret_cast<float4 *>(dst);
     const float4 *s4 = reinterpret_cast<const float4 *>(src);
 #pragma unroll
@@ -432,6 +474,7 @@ struct StoreF64x18 {
   static constexpr int NQ = 9;  // one complex number per 128-bit vector
   static constexpr bool kTwoRows = false;
   __device__ static __forceinline__ M3<double> load(const Vec *plane, int Vh, int jj) {
+    if (!in_bounds(jj, Vh, kBoundsIndex)) return m3_zero<double>();
     const Vec *p = plane + jj;
     M3<double> m;
 #pragma unroll
@@ -442,6 +485,7 @@ struct StoreF64x18 {
     return m;
   }
   __device__ static __forceinline__ M3<double> load2(const Vec *plane, int Vh, int jj) {
+    if (!in_bounds(jj, Vh, kBoundsIndex)) return m3_zero<double>();
     const Vec *p = plane + jj;
     M3<double> m;
 #pragma unroll
@@ -452,11 +496,13 @@ struct StoreF64x18 {
     return m;
   }
   __device__ static __forceinline__ void store(Vec *plane, int Vh, int jj, const M3<double> &m) {
+    if (!in_bounds(jj, Vh, kBoundsIndex)) return;
     Vec *p = plane + jj;
 #pragma unroll
     for (int q = 0; q < 9; ++q) p[q * Vh] = make_double2(m.e[q / 3][q % 3].re, m.e[q / 3][q % 3].im);
   }
   __device__ static __forceinline__ void copy(Vec *dst, int dVh, int dj, const Vec *src, int sVh, int sj) {
+    if (!(in_bounds(dj, dVh, kBoundsIndex) && in_bounds(sj, sVh, kBoundsIndex))) return;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) dst[(size_t)q * dVh + dj] = src[(size_t)q * sVh + sj];
   }
@@ -467,6 +513,10 @@ struct StoreF64x18 {
 template <class S>
 __device__ __forceinline__ typename S::Vec *plane_ptr(const ChainDesc &d, int layer, int colour, int mu) {
   typename S::Vec *base = reinterpret_cast<typename S::Vec *>(d.links);
+  // (virtual) layers: nlayers x nb sublattice boxes (nb = 1 undivided)
+  if (!(in_bounds(layer, d.nlayers * d.nb, kBoundsPlane) && in_bounds(colour, 2, kBoundsPlane) &&
+        in_bounds(mu, d.D, kBoundsPlane)))
+    return base;
   return base + ((layer * 2 + colour) * d.D + mu) * (S::NQ * d.Vh);
 }
 

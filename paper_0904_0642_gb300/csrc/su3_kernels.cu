@@ -226,11 +226,17 @@ __device__ __forceinline__ void add_staples(const ChainDesc &d, const SiteGeo &g
 // Where a form's vectors are its addressing unit (every form but the 18-real
 // float one) offset and index are summed first: one index per link.
 template <class S>
-__device__ __forceinline__ M3<typename S::R> load_at(const typename S::Vec *base, int Vh, int p, int j, bool rows2) {
+__device__ __forceinline__ M3<typename S::R> load_at(const ChainDesc &d, const typename S::Vec *base, int Vh, int p,
+                                                     int j, bool rows2) {
+  // the plane offset lies within the (virtual) layers' planes
+  if (!in_bounds(p, (long long)d.nlayers * d.nb * 2 * d.D * S::NQ * Vh, kBoundsLink)) return m3_zero<typename S::R>();
   if constexpr (std::is_same<S, StoreF32x18>::value)
     return rows2 ? S::load2(base + p, Vh, j) : S::load(base + p, Vh, j);
   else
+  {
+    if (!in_bounds(j, Vh, kBoundsIndex)) return m3_zero<typename S::R>();
     return rows2 ? S::load2(base + (p + j), Vh, 0) : S::load(base + (p + j), Vh, 0);
+  }
 }
 
 template <class S, bool WT>
@@ -238,22 +244,22 @@ __device__ __forceinline__ void add_staples_idx(const ChainDesc &d, const typena
                                                 int pc, int jc, int pa, int ja, int pf, int jf, int pe, int je, int ph,
                                                 int jh, int wu, int wl, M3<typename S::R> &A) {
   using R = typename S::R;
-  const M3<R> b = load_at<S>(base, Vh, pb, jb, false);  // U_mu(x+nu)
-  const M3<R> c = load_at<S>(base, Vh, pc, jc, true);   // U_nu(x)
+  const M3<R> b = load_at<S>(d, base, Vh, pb, jb, false);  // U_mu(x+nu)
+  const M3<R> c = load_at<S>(d, base, Vh, pc, jc, true);   // U_nu(x)
   M3<R> cb = mul_nn_2(c, b);
   third_row(cb);
-  const M3<R> a = load_at<S>(base, Vh, pa, ja, true);   // U_nu(x+mu)
+  const M3<R> a = load_at<S>(d, base, Vh, pa, ja, true);   // U_nu(x+mu)
   const bool weighted = WT && d.weighted;
   const R b0 = sizeof(R) == 4 ? (R)d.beta_f : (R)d.beta_d, b1 = sizeof(R) == 4 ? (R)d.beta1_f : (R)d.beta1_d;
   if (weighted)
     acc_su3_2rows_w(A, mul_nd_2(a, cb), wu ? b1 : b0);
   else
     acc_su3_2rows(A, mul_nd_2(a, cb));
-  const M3<R> f = load_at<S>(base, Vh, pf, jf, false);  // U_nu(x+mu-nu)
-  const M3<R> e = load_at<S>(base, Vh, pe, je, true);   // U_mu(x-nu)
+  const M3<R> f = load_at<S>(d, base, Vh, pf, jf, false);  // U_nu(x+mu-nu)
+  const M3<R> e = load_at<S>(d, base, Vh, pe, je, true);   // U_mu(x-nu)
   M3<R> ef = mul_nn_2(e, f);
   third_row(ef);
-  const M3<R> h = load_at<S>(base, Vh, ph, jh, false);  // U_nu(x-nu)
+  const M3<R> h = load_at<S>(d, base, Vh, ph, jh, false);  // U_nu(x-nu)
   if (weighted)
     acc_su3_2rows_w(A, mul_dn_2(ef, h), wl ? b1 : b0);
   else
@@ -693,15 +699,18 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) dr += __shfl_down_sync(0xffffffffu, dr, o);
       // (a warp of the ragged last tile with no valid site has no slot)
-      if ((threadIdx.x & 31) == 0 && valid && sd.action_slots)
-        atomicAdd(sd.action_slots + layer * ((sd.Vn + 31) >> 5) + (jj >> 5), sd.action_factor * (double)dr);
+      if ((threadIdx.x & 31) == 0 && valid && sd.action_slots) {
+        const int slot = layer * ((sd.Vn + 31) >> 5) + (jj >> 5);
+        if (in_bounds(slot, sd.n_action_slots, kBoundsSlot))
+          atomicAdd(sd.action_slots + slot, sd.action_factor * (double)dr);
+      }
     } else if (ss.stage == kStageReunit) {
       if (valid) reunit_site<S, SUB>(sd, layer, jj);
     } else {
       double v[kPartVals] = {0, 0, 0, 0};
       if (valid) measure_site<S, SUB>(sd, layer, jj, v);
       block_reduce(v, s_red);
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == 0 && in_bounds(lt, sd.nlayers * sd.tiles_per_layer, kBoundsPartial)) {
         for (int k = 0; k < kPartVals; ++k) sd.partials[(size_t)lt * kPartVals + k] = v[k];
         wrote_partials = true;
       }
@@ -827,7 +836,7 @@ __global__ void __launch_bounds__(256) k_measure(ChainDesc *desc_dev) {
     double v[kPartVals] = {0, 0, 0, 0};
     if (jj < d.Vh) measure_site<S>(d, layer, jj, v);
     block_reduce(v, s_red);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0 && in_bounds(lt, total, kBoundsPartial))
       for (int k = 0; k < kPartVals; ++k) d.partials[(size_t)lt * kPartVals + k] = v[k];
   }
 }
@@ -1112,7 +1121,7 @@ __global__ void __launch_bounds__(256) k_measure_noalloc(ChainDesc d, double *pa
     double v[kPartVals] = {0, 0, 0, 0};
     if (jj < d.Vh) measure_site<S>(d, layer, jj, v);
     block_reduce(v, s_red);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0 && in_bounds(lt, kNoAllocTiles, kBoundsPartial))
       for (int k = 0; k < kPartVals; ++k) partials[(size_t)lt * kPartVals + k] = v[k];
   }
 }
@@ -1204,6 +1213,35 @@ cudaError_t launch_measure_noalloc(int storage, const ChainDesc &d, int block, d
     k_measure_finalize_noalloc<<<1, 32, 0, st>>>(d, partials, out);
     return cudaGetLastError();
   });
+}
+
+// ------------------------------------------------------------------ debug bounds checks (host side)
+
+// A deliberate out-of-range index checked by the device predicate; nothing
+// is accessed, only the violation record is written.
+__global__ void k_bounds_selftest() { (void)in_bounds(1, 1, kBoundsSelfTest); }
+
+bool debug_bounds_build() {
+#ifdef SU3_DEBUG_BOUNDS
+  return true;
+#else
+  return false;
+#endif
+}
+
+cudaError_t bounds_record(unsigned long long out[3]) {
+  out[0] = out[1] = out[2] = 0;
+#ifdef SU3_DEBUG_BOUNDS
+  return cudaMemcpyFromSymbol(out, g_bounds, 3 * sizeof(unsigned long long));
+#else
+  return cudaSuccess;
+#endif
+}
+
+cudaError_t launch_bounds_selftest() {
+  k_bounds_selftest<<<1, 1>>>();
+  cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : cudaDeviceSynchronize();
 }
 
 // ------------------------------------------------------------------ launchers

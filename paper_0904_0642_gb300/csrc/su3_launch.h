@@ -39,6 +39,12 @@ cudaError_t launch_set_anchor(ChainState *state, int value, cudaStream_t st);
 // Measurement with partial sums in the library's static device scratch
 // (su3_measure_noalloc); the descriptor is passed by value.
 int noalloc_max_tiles();
+// Debug-bounds builds (SU3_DEBUG_BOUNDS): whether this is one, the first
+// recorded violation (site, index, extent; site 0: none), and a self-test
+// that records a deliberate violation without any memory access.
+bool debug_bounds_build();
+cudaError_t bounds_record(unsigned long long out[3]);
+cudaError_t launch_bounds_selftest();
 cudaError_t launch_measure_noalloc(int storage, const ChainDesc &d, int block, double *out, cudaStream_t st);
 
 }  // namespace su3g

@@ -146,3 +146,15 @@ def test_fault_sites_are_validated():
         su3.su3_inject_fault("server_round", -1)
     su3.su3_inject_fault("server_round", 0)
     su3.su3_inject_fault("server_admit", 0)
+
+
+def test_release_build_has_no_bounds_checks():
+    """The release library compiles the device bounds checks out: no
+    violation can be recorded, and the self-test is refused."""
+    if os.environ.get("SU3_DEBUG_BOUNDS") == "1":
+        pytest.skip("the debug-bounds library is loaded")
+    assert su3.su3_bounds_status() == (0, 0, 0)
+    with pytest.raises(su3.Su3Error) as ei:
+        su3.su3_bounds_selftest()
+    assert ei.value.status == su3.SU3_EINVAL
+    assert "debug bounds" not in su3.su3_version()
