@@ -270,12 +270,17 @@ __device__ __forceinline__ void add_staples_idx(const ChainDesc &d, const typena
 // once per site: forward and backward site offsets and layer flips in every
 // direction, and the plane offsets as multiples of one plane stride.  Same
 // arithmetic, same order as update_site.
-template <class S, bool WT>
+template <class S, bool WT, int DF = 0>
 __device__ __forceinline__ void update_site_lean(const ChainDesc &d, uint32_t sweep, int colour, int mu, int layer,
                                                  int jj, uint32_t &nprop, uint32_t &nacc, typename S::R &dretr) {
   using R = typename S::R;
   using Vec = typename S::Vec;
-  const int Vh = d.Vh, D = d.D;
+  // DF > 0: every chain of the launch is a periodic torus (one layer) of
+  // dimension DF, undivided, with one coupling and the default random-number
+  // site key (no layer flips, no layer offsets, D known to the compiler)
+  constexpr bool kTorus = DF > 0;
+  if constexpr (kTorus) layer = 0;
+  const int Vh = d.Vh, D = kTorus ? DF : d.D;
   const SiteGeo g = site_of<false>(d, layer, colour, jj);
   const int PS = S::NQ * Vh, CS = D * PS, LS = 2 * CS;
   const int oc = colour ^ 1;
@@ -288,6 +293,7 @@ __device__ __forceinline__ void update_site_lean(const ChainDesc &d, uint32_t sw
     if (k < D) {
       step_fwd(d, g.x[k], k, of[k], ff[k]);
       step_bwd(d, g.x[k], k, ob[k], fb[k]);
+      if constexpr (kTorus) ff[k] = fb[k] = 0;
     }
   }
   int ofm = 0, ffm = 0;
@@ -301,7 +307,7 @@ __device__ __forceinline__ void update_site_lean(const ChainDesc &d, uint32_t sw
   const int sp = s + ofm;                // x + mu
   const int pmu_oc = oc * CS + mu * PS;  // plane (oc, mu) within a layer
   const uint2 key = make_uint2(d.seed_lo, d.seed_hi);
-  const uint32_t skey = site_key<false>(d, g);
+  const uint32_t skey = kTorus ? (uint32_t)s : site_key<false>(d, g);  // the torus form has the default key
   M3<R> A = m3_zero<R>();
 #pragma unroll
   for (int nu = 0; nu < kMaxD; ++nu) {
@@ -654,7 +660,11 @@ template <> struct TickBounds<10> { static constexpr int kThreads = 256, kMinBlo
 // beta1 != beta); unweighted chains compute identically in both forms.
 // SUB: compiled for a chain divided into sublattice boxes (one chain per
 // engine); a halo refresh follows every launch.
-template <class S, int V, bool WT, bool SUB = false>
+// TOR: compiled for engines whose chains are all undivided periodic 4-D tori
+// with one coupling and the default random-number key (the benchmark's
+// lattices and most ensembles): the unrolled update with D, the layer and
+// the site key fixed at compile time.
+template <class S, int V, bool WT, bool SUB = false, bool TOR = false>
 __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBlocks) k_tick(EngineArgs ea) {
   __shared__ ChainDesc sd;
   __shared__ ChainState ss;
@@ -688,7 +698,9 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
       const int colour = ss.stage / sd.D, mu = ss.stage - colour * sd.D;
       typename S::R dr = 0;  // change of Re Tr(U A), in the kernel's precision
       if (valid) {
-        if constexpr (!TickBounds<V>::kRolled && !SUB)
+        if constexpr (TOR)
+          update_site_lean<S, false, 4>(sd, ss.sweep, colour, mu, layer, jj, np, na, dr);
+        else if constexpr (!TickBounds<V>::kRolled && !SUB)
           update_site_lean<S, WT>(sd, ss.sweep, colour, mu, layer, jj, np, na, dr);
         else
           update_site<S, TickBounds<V>::kRolled, WT, SUB>(sd, ss.sweep, colour, mu, layer, jj, np, na, dr);
@@ -1256,10 +1268,10 @@ int tick_variants(int storage) { return storage == 1 ? 5 : 1; }
 // pdl: launch as a programmatic dependent of the previous kernel in the
 // stream (the tick waits for that kernel's completion and memory at its
 // first instruction, so only the launch itself overlaps the previous tick).
-template <class S, int V, bool WT, bool SUB = false>
+template <class S, int V, bool WT, bool SUB = false, bool TOR = false>
 static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_t st, bool pdl) {
   if (!pdl) {
-    k_tick<S, V, WT, SUB><<<grid, block, 0, st>>>(ea);
+    k_tick<S, V, WT, SUB, TOR><<<grid, block, 0, st>>>(ea);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -1272,12 +1284,12 @@ static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_tick<S, V, WT, SUB>, ea);
+  return cudaLaunchKernelEx(&cfg, k_tick<S, V, WT, SUB, TOR>, ea);
 }
 
-template <class S, int V, bool WT, bool SUB = false>
+template <class S, int V, bool WT, bool SUB = false, bool TOR = false>
 static cudaError_t occ_v(int block, int *ctas) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<S, V, WT, SUB>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<S, V, WT, SUB, TOR>, block, 0);
 }
 
 int tick_max_threads(int storage, int variant) {
@@ -1292,41 +1304,46 @@ int tick_max_threads(int storage, int variant) {
   }
 }
 
-// One switch for launching and for occupancy queries: OP<S, V, WT, SUB>.
-template <template <class, int, bool, bool> class OP, bool WT, class... A>
-static cudaError_t tick_dispatch(int storage, int variant, bool sub, A... a) {
-  if (storage == 0) return sub ? OP<StoreF64x18, 10, WT, true>::run(a...) : OP<StoreF64x18, 10, WT, false>::run(a...);
-  if (storage == 2)
-    return sub ? OP<StoreF32x18, kSubVariant, WT, true>::run(a...) : OP<StoreF32x18, 0, WT, false>::run(a...);
-  if (sub) return OP<StoreF32x12, kSubVariant, WT, true>::run(a...);
+// One switch for launching and for occupancy queries: OP<S, V, WT, SUB, TOR>.
+// The torus form exists for the unrolled float variants (FP32 12-real 0 and
+// 1, FP32 18-real 0); the others ignore `tor`.
+template <template <class, int, bool, bool, bool> class OP, bool WT, class... A>
+static cudaError_t tick_dispatch(int storage, int variant, bool sub, bool tor, A... a) {
+  tor = tor && !sub && !WT;
+  if (storage == 0) return sub ? OP<StoreF64x18, 10, WT, true, false>::run(a...) : OP<StoreF64x18, 10, WT, false, false>::run(a...);
+  if (storage == 2) {
+    if (sub) return OP<StoreF32x18, kSubVariant, WT, true, false>::run(a...);
+    return tor ? OP<StoreF32x18, 0, false, false, true>::run(a...) : OP<StoreF32x18, 0, WT, false, false>::run(a...);
+  }
+  if (sub) return OP<StoreF32x12, kSubVariant, WT, true, false>::run(a...);
   switch (variant) {
-    case 0: return OP<StoreF32x12, 0, WT, false>::run(a...);
-    case 1: return OP<StoreF32x12, 1, WT, false>::run(a...);
-    case 2: return OP<StoreF32x12, 2, WT, false>::run(a...);
-    case 3: return OP<StoreF32x12, 3, WT, false>::run(a...);
-    default: return OP<StoreF32x12, 4, WT, false>::run(a...);
+    case 0: return tor ? OP<StoreF32x12, 0, false, false, true>::run(a...) : OP<StoreF32x12, 0, WT, false, false>::run(a...);
+    case 1: return tor ? OP<StoreF32x12, 1, false, false, true>::run(a...) : OP<StoreF32x12, 1, WT, false, false>::run(a...);
+    case 2: return OP<StoreF32x12, 2, WT, false, false>::run(a...);
+    case 3: return OP<StoreF32x12, 3, WT, false, false>::run(a...);
+    default: return OP<StoreF32x12, 4, WT, false, false>::run(a...);
   }
 }
 
-template <class S, int V, bool WT, bool SUB>
+template <class S, int V, bool WT, bool SUB, bool TOR>
 struct TickLaunch {
   static cudaError_t run(const EngineArgs *ea, int grid, int block, cudaStream_t st, bool pdl) {
-    return tick_v<S, V, WT, SUB>(*ea, grid, block, st, pdl);
+    return tick_v<S, V, WT, SUB, TOR>(*ea, grid, block, st, pdl);
   }
 };
 
-template <class S, int V, bool WT, bool SUB>
+template <class S, int V, bool WT, bool SUB, bool TOR>
 struct TickOccupancy {
-  static cudaError_t run(int block, int *ctas) { return occ_v<S, V, WT, SUB>(block, ctas); }
+  static cudaError_t run(int block, int *ctas) { return occ_v<S, V, WT, SUB, TOR>(block, ctas); }
 };
 
-cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, const EngineArgs &ea, int grid, int block,
-                        cudaStream_t st, bool pdl) {
+cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, bool torus, const EngineArgs &ea, int grid,
+                        int block, cudaStream_t st, bool pdl) {
   if (sub) variant = storage == 0 ? 0 : kSubVariant;
   if (block > tick_max_threads(storage, variant)) return cudaErrorInvalidConfiguration;
   const EngineArgs *pa = &ea;
-  return weighted ? tick_dispatch<TickLaunch, true>(storage, variant, sub, pa, grid, block, st, pdl)
-                  : tick_dispatch<TickLaunch, false>(storage, variant, sub, pa, grid, block, st, pdl);
+  return weighted ? tick_dispatch<TickLaunch, true>(storage, variant, sub, torus, pa, grid, block, st, pdl)
+                  : tick_dispatch<TickLaunch, false>(storage, variant, sub, torus, pa, grid, block, st, pdl);
 }
 
 cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, int all, int boxes,
@@ -1387,12 +1404,12 @@ cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, doub
   });
 }
 
-cudaError_t tick_occupancy(int storage, int variant, bool weighted, bool sub, int block, int *ctas_per_sm) {
+cudaError_t tick_occupancy(int storage, int variant, bool weighted, bool sub, bool torus, int block, int *ctas_per_sm) {
   *ctas_per_sm = 0;
   if (sub) variant = storage == 0 ? 0 : kSubVariant;
   if (block > tick_max_threads(storage, variant)) return cudaSuccess;
-  return weighted ? tick_dispatch<TickOccupancy, true>(storage, variant, sub, block, ctas_per_sm)
-                  : tick_dispatch<TickOccupancy, false>(storage, variant, sub, block, ctas_per_sm);
+  return weighted ? tick_dispatch<TickOccupancy, true>(storage, variant, sub, torus, block, ctas_per_sm)
+                  : tick_dispatch<TickOccupancy, false>(storage, variant, sub, torus, block, ctas_per_sm);
 }
 
 void host_advance_stage(const ChainDesc &d, ChainState &s) { advance_stage(d, s); }
