@@ -389,30 +389,111 @@ __device__ __forceinline__ M3<double> load_rows2_d(const typename S::Vec *p, int
   return m;
 }
 
+// The double-precision Gram-Schmidt of two float rows r1, r2, applied in
+// float.  The norms and the inner product are summed in double from the
+// float elements (products of floats are exact in double):
+//   n1 = |r1|^2, s1 = n1^(-1/2), q = <r1, r2>, p = s1 q = <r1', r2>,
+//   n2 = |r2 - p r1'|^2 = |r2|^2 - |p|^2 (as |r1'| = 1), s2 = n2^(-1/2).
+// The results r1' = r1 s1 and r2'' = (r2 - p r1') s2 differ from the stored
+// rows by corrections of the rows' departure from orthonormality (~1e-7
+// between re-unitarisations): r1' = r1 + r1 e1 with e1 = s1 - 1, and
+// r2'' = r2 + (c (1 + e2) + r2 e2) with c = -p r1' and e2 = s2 - 1.  Each
+// correction is formed in float (the factors e1, p, e2 rounded to float:
+// relative errors 2^-24 of small quantities) and added with a single
+// rounding, so the stored floats are the double computation's rounded
+// result except where that result lies within ~1e-14 of a rounding boundary
+// (1e-12 for departures of 1e-4).  38 double operations per link instead of
+// 56, on a pipe that runs at 1/64 of the float rate here.
+__device__ __forceinline__ void reunit_rows2_f(M3<float> &m) {
+  C<float> *r1 = m.e[0], *r2 = m.e[1];
+  double n1 = f2d_bits(r1[0].re) * f2d_bits(r1[0].re);
+  n1 = fm(f2d_bits(r1[0].im), f2d_bits(r1[0].im), n1);
+  double n2 = f2d_bits(r2[0].re) * f2d_bits(r2[0].re);
+  n2 = fm(f2d_bits(r2[0].im), f2d_bits(r2[0].im), n2);
+  // q = sum_k conj(r1_k) r2_k
+  double qr = f2d_bits(r1[0].re) * f2d_bits(r2[0].re), qi = f2d_bits(r1[0].re) * f2d_bits(r2[0].im);
+  qr = fm(f2d_bits(r1[0].im), f2d_bits(r2[0].im), qr);
+  qi = fm(-f2d_bits(r1[0].im), f2d_bits(r2[0].re), qi);
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    const double ar = f2d_bits(r1[k].re), ai = f2d_bits(r1[k].im), br = f2d_bits(r2[k].re), bi = f2d_bits(r2[k].im);
+    n1 = fm(ar, ar, n1);
+    n1 = fm(ai, ai, n1);
+    n2 = fm(br, br, n2);
+    n2 = fm(bi, bi, n2);
+    qr = fm(ar, br, qr);
+    qr = fm(ai, bi, qr);
+    qi = fm(ar, bi, qi);
+    qi = fm(-ai, br, qi);
+  }
+  const double s1 = rsqrt_d<1>(n1);
+  const double pdr = s1 * qr, pdi = s1 * qi;
+  n2 = fm(-pdr, pdr, n2);
+  n2 = fm(-pdi, pdi, n2);
+  const double s2 = rsqrt_d<1>(n2);
+  const float e1 = d2f_bits(s1 - 1.0), e2 = d2f_bits(s2 - 1.0);
+  const float pr = d2f_bits(pdr), pi = d2f_bits(pdi);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const C<float> a = r1[k];
+    r1[k] = {fm(a.re, e1, a.re), fm(a.im, e1, a.im)};
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    // c = -p r1'_k, then r2''_k = r2_k + (c (1 + e2) + r2_k e2), one rounding
+    const C<float> a = r1[k], b = r2[k];
+    const float cr = fm(pi, a.im, -pr * a.re), ci = fm(-pi, a.re, -pr * a.im);
+    r2[k] = {b.re + fm(b.re, e2, fm(cr, e2, cr)), b.im + fm(b.im, e2, fm(ci, e2, ci))};
+  }
+}
+
 // Two links per step: their Gram-Schmidt chains are independent.
 template <class S, bool SUB = false>
 __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int jj) {
   constexpr bool kTwoRows = S::kTwoRows;  // the 12-real form keeps rows 1, 2 only
   constexpr int kNewton = sizeof(typename S::R) == 4 ? 1 : 2;  // float storage: one Newton step suffices
   const int Vh = d.Vh;
-  for (int colour = 0; colour < 2; ++colour) {
-    const int js = SUB ? (site_of<true>(d, layer, colour, jj).s >> 1) : jj;
-    int mu = 0;
+  if constexpr (std::is_same<S, StoreF32x12>::value) {
+    // two-row float storage: the double Gram-Schmidt applied in float
+    for (int colour = 0; colour < 2; ++colour) {
+      const int js = SUB ? (site_of<true>(d, layer, colour, jj).s >> 1) : jj;
+      int mu = 0;
 #pragma unroll 1
-    for (; mu + 1 < d.D; mu += 2) {
-      typename S::Vec *p0 = plane_ptr<S>(d, layer, colour, mu), *p1 = plane_ptr<S>(d, layer, colour, mu + 1);
-      M3<double> m0 = load_rows2_d<S>(p0, Vh, js);
-      M3<double> m1 = load_rows2_d<S>(p1, Vh, js);
-      reunit_d<kNewton, !kTwoRows>(m0);
-      reunit_d<kNewton, !kTwoRows>(m1);
-      S::store(p0, Vh, js, to_storage<typename S::R>(m0));
-      S::store(p1, Vh, js, to_storage<typename S::R>(m1));
+      for (; mu + 1 < d.D; mu += 2) {
+        typename S::Vec *p0 = plane_ptr<S>(d, layer, colour, mu), *p1 = plane_ptr<S>(d, layer, colour, mu + 1);
+        M3<float> m0 = S::load2(p0, Vh, js), m1 = S::load2(p1, Vh, js);
+        reunit_rows2_f(m0);
+        reunit_rows2_f(m1);
+        S::store(p0, Vh, js, m0);
+        S::store(p1, Vh, js, m1);
+      }
+      if (mu < d.D) {
+        typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
+        M3<float> m = S::load2(p, Vh, js);
+        reunit_rows2_f(m);
+        S::store(p, Vh, js, m);
+      }
     }
-    if (mu < d.D) {
-      typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
-      M3<double> m = load_rows2_d<S>(p, Vh, js);
-      reunit_d<kNewton, !kTwoRows>(m);
-      S::store(p, Vh, js, to_storage<typename S::R>(m));
+  } else {
+    for (int colour = 0; colour < 2; ++colour) {
+      const int js = SUB ? (site_of<true>(d, layer, colour, jj).s >> 1) : jj;
+      int mu = 0;
+#pragma unroll 1
+      for (; mu + 1 < d.D; mu += 2) {
+        typename S::Vec *p0 = plane_ptr<S>(d, layer, colour, mu), *p1 = plane_ptr<S>(d, layer, colour, mu + 1);
+        M3<double> m0 = load_rows2_d<S>(p0, Vh, js);
+        M3<double> m1 = load_rows2_d<S>(p1, Vh, js);
+        reunit_d<kNewton, !kTwoRows>(m0);
+        reunit_d<kNewton, !kTwoRows>(m1);
+        S::store(p0, Vh, js, to_storage<typename S::R>(m0));
+        S::store(p1, Vh, js, to_storage<typename S::R>(m1));
+      }
+      if (mu < d.D) {
+        typename S::Vec *p = plane_ptr<S>(d, layer, colour, mu);
+        M3<double> m = load_rows2_d<S>(p, Vh, js);
+        reunit_d<kNewton, !kTwoRows>(m);
+        S::store(p, Vh, js, to_storage<typename S::R>(m));
+      }
     }
   }
 }
@@ -422,13 +503,17 @@ __device__ __forceinline__ void reunit_site(const ChainDesc &d, int layer, int j
 // in double: plaquettes split space/time, and Polyakov lines started at
 // x^D = 0 (the line follows the forward time neighbour until it closes).
 
-// Re Tr(U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+) = sum_ij Re(P_ij
-// conj(Q_ij)) with P = U_mu(x) U_nu(x+mu), Q = U_nu(x) U_mu(x+nu), taken row
-// by row so that few values are live at once; um = U_mu(x) is loaded once
-// by the caller for all nu.  The factor 1/3 is applied to the sums.
+// Re Tr(U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+) = Re Tr(P Q^+) with
+// P = U_mu(x) U_nu(x+mu), Q = U_nu(x) U_mu(x+nu), both in SU(3): rows 1, 2
+// of P and Q come from rows 1, 2 of U_mu(x) and U_nu(x) (um2, un2) and the
+// full U_nu(x+mu), U_mu(x+nu); their third rows contribute
+// sum_j P_3j conj(Q_3j) = <P_1 x P_2, Q_1 x Q_2> = G_11 G_22 - G_12 G_21
+// (the Binet-Cauchy identity; row 3 of an SU(3) matrix is the conjugated
+// cross product of rows 1, 2) with G_kl = <P_k, Q_l> = sum_j conj(P_kj) Q_lj.
+// The factor 1/3 is applied to the sums.
 template <class S, bool SUB = false>
-__device__ __forceinline__ double plaquette_at(const ChainDesc &d, const SiteGeo &g, int colour, int mu, int nu,
-                                               int xmu, int xnu, const M3<typename S::R> &um) {
+__device__ __forceinline__ typename S::R plaquette_at(const ChainDesc &d, const SiteGeo &g, int colour, int mu, int nu,
+                                                      int xmu, int xnu, const M3<typename S::R> &um2) {
   using R = typename S::R;
   const int Vh = d.Vh, layer = g.layer, jj = g.s >> 1, oc = colour ^ 1;
   int offp, flp, offn, fln;
@@ -436,30 +521,32 @@ __device__ __forceinline__ double plaquette_at(const ChainDesc &d, const SiteGeo
   step_fwd(d, xnu, nu, offn, fln);
   const M3<R> a = S::load(plane_ptr<S>(d, lflip<SUB>(d, layer, flp), oc, nu), Vh, (g.s + offp) >> 1);  // U_nu(x+mu)
   const M3<R> b = S::load(plane_ptr<S>(d, lflip<SUB>(d, layer, fln), oc, mu), Vh, (g.s + offn) >> 1);  // U_mu(x+nu)
-  const M3<R> un = S::load(plane_ptr<S>(d, layer, colour, nu), Vh, jj);                  // U_nu(x)
-  R tr = R(0);
+  const M3<R> un2 = S::load2(plane_ptr<S>(d, layer, colour, nu), Vh, jj);                // U_nu(x), rows 1, 2
+  const M3<R> P = mul_nn_2(um2, a), Q = mul_nn_2(un2, b);
+  C<R> G[2][2];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    // row i of P and Q
+  for (int k = 0; k < 2; ++k)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      C<R> p = cmul(um.e[i][0], a.e[0][j]);
-      cmac(p, um.e[i][1], a.e[1][j]);
-      cmac(p, um.e[i][2], a.e[2][j]);
-      C<R> q = cmul(un.e[i][0], b.e[0][j]);
-      cmac(q, un.e[i][1], b.e[1][j]);
-      cmac(q, un.e[i][2], b.e[2][j]);
-      tr = fm(p.re, q.re, tr);
-      tr = fm(p.im, q.im, tr);
+    for (int l = 0; l < 2; ++l) {
+      C<R> x = cmul_cn(P.e[k][0], Q.e[l][0]);
+      cmac_cn(x, P.e[k][1], Q.e[l][1]);
+      cmac_cn(x, P.e[k][2], Q.e[l][2]);
+      G[k][l] = x;
     }
-  }
-  return to_double(tr);
+  R tr = G[0][0].re + G[1][1].re;
+  tr = fm(G[0][0].re, G[1][1].re, tr);
+  tr = fm(-G[0][0].im, G[1][1].im, tr);
+  tr = fm(-G[0][1].re, G[1][0].re, tr);
+  tr = fm(G[0][1].im, G[1][0].im, tr);
+  return tr;
 }
 
 // Per thread: the two sites of checkerboard index jj (both colours).  Sums
-// in double of Re Tr and Tr (the 1/3 is applied by finalize_measure):
-// plaquettes split space/time, and Polyakov lines started at x^D = 0 (the
-// line follows the forward time neighbour until it closes).
+// of Re Tr and Tr (the 1/3 is applied by finalize_measure): plaquettes split
+// space/time, summed per site in the storage precision and accumulated in
+// double; Polyakov lines started at x^D = 0 (the line follows the forward
+// time neighbour until it closes).  The loop over mu is unrolled so that
+// the loads of several plaquettes are in flight together.
 // SUB: plaquettes read the forward halos; a Polyakov line stays inside its
 // sublattice box only when time is undivided, so it is taken only then.
 template <class S, bool SUB = false>
@@ -470,37 +557,49 @@ __device__ __forceinline__ void measure_site(const ChainDesc &d, int layer, int 
 #pragma unroll 1
   for (int colour = 0; colour < 2; ++colour) {
     const SiteGeo g = site_of<SUB>(d, layer, colour, jj);
-#pragma unroll 1
-    for (int mu = 0; mu + 1 < D; ++mu) {
+    R ps = R(0), pt = R(0);
+#pragma unroll
+    for (int mu = 0; mu + 1 < kMaxD; ++mu) {
+      if (mu + 1 >= D) continue;
       const int xmu = sel(g.x, mu);
-      const M3<R> um = S::load(plane_ptr<S>(d, layer, colour, mu), Vh, g.s >> 1);  // U_mu(x)
-      // unrolled over a fixed bound so that the loads of the plaquettes
-      // of this mu can be in flight together
+      const M3<R> um2 = S::load2(plane_ptr<S>(d, layer, colour, mu), Vh, g.s >> 1);  // U_mu(x), rows 1, 2
 #pragma unroll
       for (int nu = 1; nu < kMaxD; ++nu) {
         if (nu <= mu || nu >= D) continue;
-        const double p = plaquette_at<S, SUB>(d, g, colour, mu, nu, xmu, g.x[nu], um);
-        if (nu == D - 1) acc[1] += p; else acc[0] += p;
+        const R p = plaquette_at<S, SUB>(d, g, colour, mu, nu, xmu, g.x[nu], um2);
+        if (nu == D - 1) pt += p; else ps += p;
       }
     }
+    acc[0] += to_double(ps);
+    acc[1] += to_double(pt);
     const int t = D - 1;
     if (sel(g.x, t) == 0 && !(SUB && d.hpad[t])) {
-      // Polyakov line through (layer, x, x^D = 0)
-      M3<R> P = S::load(plane_ptr<S>(d, layer, colour, t), Vh, g.s >> 1);
+      // Polyakov line through (layer, x, x^D = 0): rows 1, 2 of the running
+      // product (SU(3)), the next link's load issued before the product
+      M3<R> P = S::load2(plane_ptr<S>(d, layer, colour, t), Vh, g.s >> 1);
       int cs = g.s, cl = layer, cc = colour, xt = 0;
-#pragma unroll 1
-      for (int step = 0; step < 2 * d.dims[t]; ++step) {
+      auto advance = [&]() {
         int off, fl;
         step_fwd(d, xt, t, off, fl);
         cs += off;
         cl = lflip<SUB>(d, cl, fl);
         cc ^= 1;
         xt = (xt == d.dims[t] - 1) ? 0 : xt + 1;
-        if (cs == g.s && cl == layer) break;
-        P = mul_nn(P, S::load(plane_ptr<S>(d, cl, cc, t), Vh, cs >> 1));
+        return !(cs == g.s && cl == layer);
+      };
+      bool more = advance();
+      M3<R> nxt = more ? S::load(plane_ptr<S>(d, cl, cc, t), Vh, cs >> 1) : m3_zero<R>();
+#pragma unroll 1
+      while (more) {
+        const M3<R> cur = nxt;
+        more = advance();
+        if (more) nxt = S::load(plane_ptr<S>(d, cl, cc, t), Vh, cs >> 1);
+        P = mul_nn_2(P, cur);
       }
-      acc[2] += to_double(P.e[0][0].re + P.e[1][1].re + P.e[2][2].re);
-      acc[3] += to_double(P.e[0][0].im + P.e[1][1].im + P.e[2][2].im);
+      // trace: P_11 + P_22 + P_33 with P_33 = conj(P_11 P_22 - P_12 P_21)
+      const C<R> p33 = conj_cross(P.e[0][0], P.e[1][1], P.e[0][1], P.e[1][0]);
+      acc[2] += to_double(P.e[0][0].re + P.e[1][1].re + p33.re);
+      acc[3] += to_double(P.e[0][0].im + P.e[1][1].im + p33.im);
     }
   }
 }
