@@ -114,7 +114,7 @@ def float_start(U):
 
 
 def test_served_jobs_match_the_oracle():
-    """Jobs submitted while others run (the benchmark spec serving clause; Sec. 2.1
+    """Jobs submitted while others run (continuous batching; the Sec. 2.1
     update): after one sweep every link against the oracle as in the FP32
     parity tests, the proposal and acceptance counts equal unless a decision
     sits at its threshold; after three sweeps the plaquette (total, per
