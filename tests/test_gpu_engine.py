@@ -147,32 +147,46 @@ def test_measurement_stage_records_every_k_sweeps():
     assert np.allclose(m[:, 0], m[:, 1])  # one layer: the layer slot equals the whole lattice
 
 
-@pytest.mark.parametrize("storage,tol", [(su3.SU3_FP64_18, 1e-11), (su3.SU3_FP32_12, 1e-5), (su3.SU3_FP32_18, 1e-5)])
-def test_full_size_sampled_links(storage, tol):
-    """32^4, beta = 6, hot start, one sweep at the benchmark's launch shape:
+FULL_SIZE = [  # (dims, layers, glue_mask, beta, storage, tol): the benchmark lattice and both config-3 workloads
+    ([32, 32, 32, 32], 1, 0, 6.0, su3.SU3_FP64_18, 1e-11),
+    ([32, 32, 32, 32], 1, 0, 6.0, su3.SU3_FP32_12, 1e-5),
+    ([32, 32, 32, 32], 1, 0, 6.0, su3.SU3_FP32_18, 1e-5),
+    ([16, 16, 16, 4], 2, 0b1000, 5.7, su3.SU3_FP32_12, 1e-5),   # two 16^3 x 4 layers glued in time
+    ([16, 16, 16, 4], 2, 0b1000, 5.7, su3.SU3_FP64_18, 1e-11),
+    ([64, 64, 64], 1, 0, 10.0, su3.SU3_FP32_12, 1e-5),           # D = 3
+]
+
+
+@pytest.mark.parametrize("dims,layers,glue,beta,storage,tol", FULL_SIZE,
+                         ids=lambda v: "x".join(map(str, v)) if isinstance(v, list) else str(v))
+def test_full_size_sampled_links(dims, layers, glue, beta, storage, tol):
+    """Full-size lattices, hot start, one sweep at the default launch shape:
     links of the first phase (colour 0, direction 1) were updated from the
-    start configuration, links of the last phase (colour 1, direction 4) from
+    start configuration, links of the last phase (colour 1, direction D) from
     the final configuration of all other links.  The oracle recomputes a
-    sample of both, link by link."""
-    dims = [32, 32, 32, 32]
-    lat = su3.Lattice(dims, beta=6.0, seed=20090406, storage=storage, start=su3.SU3_START_HOT, hits=2)
+    sample of both, in every layer, link by link (the random-number site key
+    is layer * V + i_s - 1)."""
+    boundary = su3.SU3_DLT if layers == 2 else su3.SU3_PBC
+    lat = su3.Lattice(dims, boundary=boundary, glue_mask=glue, beta=beta, seed=20090406, storage=storage,
+                      start=su3.SU3_START_HOT, hits=2)
     c0 = lat.get_links()
     lat.sweep(1)
     c1 = lat.get_links()
-    o = oracle.Lattice(dims)
+    lat.close()
+    o = oracle.Lattice(dims, nlayers=layers, glue_mask=glue or None)
+    D = len(dims)
     rng = np.random.default_rng(0)
     checked = bad = 0
-    for phase, mu, src in ((0, 0, c0), (1, 3, c1)):
+    for phase, mu, src in ((0, 0, c0), (1, D - 1, c1)):
         o.U[...] = src
-        sites = rng.integers(0, o.V, 400)
-        for s in sites:
-            x = o.site_coords(int(s))
-            if sum(x) % 2 != phase:
+        for layer, s in zip(rng.integers(0, layers, 400), rng.integers(0, o.V, 400)):
+            layer, s = int(layer), int(s)
+            if sum(o.site_coords(s)) % 2 != phase:
                 continue
-            A = o.staple(0, int(s), mu)
-            old = oracle.to_complex(c0[0, s, mu])
-            new, _ = oracle.link_heatbath(old, A, 6.0, 2, 20090406, int(s), 0, phase, mu)
-            err = np.max(np.abs(oracle.from_complex(new) - c1[0, s, mu]))
+            A = o.staple(layer, s, mu)
+            old = oracle.to_complex(c0[layer, s, mu])
+            new, _ = oracle.link_heatbath(old, A, beta, 2, 20090406, layer * o.V + s, 0, phase, mu)
+            err = np.max(np.abs(oracle.from_complex(new) - c1[layer, s, mu]))
             checked += 1
             bad += err > tol
     assert checked > 300

@@ -41,7 +41,11 @@ def test_jobs_in_the_mix_equal_jobs_alone():
         ids.append(srv.submit(job_config(i, dims, b, beta), sweeps))
         time.sleep(0.002)  # arrivals while earlier jobs run
     results = [srv.wait(j, timeout_s=120) for j in ids]
+    rounds, device_ms = srv.stats()
     srv.close()
+    # every job's ticks ran inside the worker's rounds, timed on the device
+    assert rounds >= max(sweeps for *_, sweeps in JOBS) * 2 * 4 // 16
+    assert 0.0 < device_ms < 1e3 * max(r.finish_s for r in results)
     for i, ((dims, b, beta, sweeps), r) in enumerate(zip(JOBS, results)):
         assert r.status == su3.SU3_OK
         plaq, poly, (prop, acc, _) = alone(i, dims, b, beta, sweeps)
