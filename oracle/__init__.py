@@ -75,7 +75,7 @@ def _configure(L):
     L.orc_cold_start.argtypes = [gp, dp]
     L.orc_hot_start.argtypes = [gp, c_uint64, dp]
     L.orc_staple.argtypes = [gp, dp, c_int, c_int64, c_int, dp]
-    L.orc_su2_samples.argtypes = [c_double, c_int, c_uint64, c_int64, dp, POINTER(c_int32)]
+    L.orc_su2_samples.argtypes = [c_double, c_int, c_uint64, c_int64, c_int, dp, POINTER(c_int32)]
     L.orc_link_heatbath.argtypes = [dp, dp, c_double, c_int, c_uint64, c_uint32, c_uint32, c_int, c_int,
                                     POINTER(c_uint64)]
     L.orc_link_chain.argtypes = [dp, dp, c_double, c_int, c_uint64, c_int64, dp]
@@ -150,11 +150,12 @@ def philox4x32_10(ctr, key):
     return [int(v) for v in o]
 
 
-def su2_samples(alpha: float, hits: int, seed: int, n: int):
-    """n SU(2) heatbath draws at fixed alpha; returns (x[n,4], accepted[n])."""
+def su2_samples(alpha: float, hits: int, seed: int, n: int, subgroup: int = 0):
+    """n SU(2) heatbath draws of one subgroup (0, 1, 2) at fixed alpha, draw i
+    at counter (i, 0); returns (x[n,4], accepted[n])."""
     x = np.zeros((n, 4), dtype=np.float64)
     acc = np.zeros(n, dtype=np.int32)
-    lib().orc_su2_samples(alpha, hits, seed, n, _dp(x), acc.ctypes.data_as(POINTER(c_int32)))
+    lib().orc_su2_samples(alpha, hits, seed, n, subgroup, _dp(x), acc.ctypes.data_as(POINTER(c_int32)))
     return x, acc.astype(bool)
 
 

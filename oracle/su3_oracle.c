@@ -436,6 +436,10 @@ void orc_staple_weighted(const orc_geom *g, const double *U, int layer, int64_t 
 /*   on acceptance two more uniforms u5, u6 give the direction of         */
 /*   (x1,x2,x3), of length sqrt(1 - x0^2) = sqrt(X (2 - X)):              */
 /*     cos(theta) = 2 u5 - 1, phi = 2 pi u6.                              */
+/*   u5, u6 are two words of a direction block: subgroups 1 and 2 (of the */
+/*   three, counted from 0: subgroups 0 and 1) share the block of         */
+/*   subgroup 0, the first taking its words 1, 2 and the second words     */
+/*   3, 4; subgroup 2 takes words 1, 2 of its own block.                  */
 /* ------------------------------------------------------------------ */
 
 typedef struct {
@@ -466,10 +470,12 @@ static orc_su2_draw_t orc_su2_draw(double alpha, int hits, uint64_t seed, uint32
   }
   if (!r.accepted) return r;
   double u[4];
-  orc_draw(seed, c0, c1, orc_tag(colour, mu, subgroup, ORC_HIT_DIRECTION), ORC_PURPOSE_HEATBATH, u);
-  double costh = 2.0 * u[0] - 1.0;
+  orc_draw(seed, c0, c1, orc_tag(colour, mu, subgroup == 1 ? 0 : subgroup, ORC_HIT_DIRECTION), ORC_PURPOSE_HEATBATH,
+           u);
+  double u5 = subgroup == 1 ? u[2] : u[0], u6 = subgroup == 1 ? u[3] : u[1];
+  double costh = 2.0 * u5 - 1.0;
   double sinth = sqrt(1.0 - costh * costh);
-  double phi = ORC_TWO_PI * u[1];
+  double phi = ORC_TWO_PI * u6;
   double rho = sqrt(X * (2.0 - X));
   r.x[0] = 1.0 - X;
   r.x[1] = rho * sinth * cos(phi);
@@ -486,11 +492,12 @@ static void su2_matrix(const double a[4], cplx m[2][2]) {
   m[1][1] = a[0] - I * a[3];
 }
 
-/* Test hook: n independent draws (counter (i, 0, tag(0,0,0,h))) of the SU(2)
- * heatbath at fixed alpha, with the same routine the sweep uses. */
-void orc_su2_samples(double alpha, int hits, uint64_t seed, int64_t n, double *x, int32_t *accepted) {
+/* Test hook: n independent draws (counter (i, 0, tag(0,0,subgroup,h))) of the
+ * SU(2) heatbath of one subgroup at fixed alpha, with the same routine the
+ * sweep uses. */
+void orc_su2_samples(double alpha, int hits, uint64_t seed, int64_t n, int subgroup, double *x, int32_t *accepted) {
   for (int64_t i = 0; i < n; ++i) {
-    orc_su2_draw_t r = orc_su2_draw(alpha, hits, seed, (uint32_t)i, (uint32_t)(i >> 32), 0, 0, 0);
+    orc_su2_draw_t r = orc_su2_draw(alpha, hits, seed, (uint32_t)i, (uint32_t)(i >> 32), 0, 0, subgroup);
     for (int k = 0; k < 4; ++k) x[4 * i + k] = r.x[k];
     accepted[i] = r.accepted;
   }

@@ -576,6 +576,17 @@ __device__ __forceinline__ uint32_t heatbath_tag(int colour, int mu, int subgrou
   return ((uint32_t)subgroup << 8) | ((uint32_t)mu << 10) | ((uint32_t)colour << 14);
 }
 
+// The two uniforms of a subgroup's direction are two words of a direction
+// block: subgroups 0 and 1 share the block of subgroup 0 (words x, y and
+// z, w), subgroup 2 takes words x, y of its own.  Five blocks per link
+// update when every first proposal is accepted, not six.
+__device__ __forceinline__ uint2 direction_words(uint2 key, uint32_t c0, uint32_t c1, uint32_t tag) {
+  const uint32_t sg = (tag >> 8) & 3u;
+  const uint32_t block_tag = (tag & ~(3u << 8)) | ((sg & 2u) << 8) | kHitDirection;
+  const uint4 v = philox4x32_10(make_uint4(c0, c1, block_tag, kPurposeHeatbath), key);
+  return sg == 1 ? make_uint2(v.z, v.w) : make_uint2(v.x, v.y);
+}
+
 // ------------------------------------------------------------------ SU(2) heatbath
 // Kennedy-Pendleton with the Fredenhagen-Marcu hit limit: per hit
 // X = -(ln u1 + cos^2(2 pi u2) ln u3) / alpha, accepted when
@@ -598,7 +609,7 @@ __device__ __forceinline__ bool su2_draw_d(double alpha, int hits, uint2 key, ui
     }
   }
   if (!acc) return false;
-  const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | kHitDirection, kPurposeHeatbath), key);
+  const uint2 w = direction_words(key, c0, c1, tag);
   const double costh = 2.0 * unif_d(w.x) - 1.0;
   const double sinth = sqrt(1.0 - costh * costh);
   double sphi, cphi;
@@ -653,7 +664,7 @@ __device__ __forceinline__ bool su2_draw_f(float alpha, int hits, uint2 key, uin
     }
   }
   if (!acc) return false;
-  const uint4 w = philox4x32_10(make_uint4(c0, c1, tag | kHitDirection, kPurposeHeatbath), key);
+  const uint2 w = direction_words(key, c0, c1, tag);
   const float costh = 2.0f * unif_f(w.x) - 1.0f;
   const float sinth = sqrt_sfu(1.0f - costh * costh);
   float sphi, cphi;
@@ -777,7 +788,7 @@ __device__ __forceinline__ void cm_update(M3<R> &U, const M3<R> &A, R beta, int 
 // alone.  So are the parts of the proposal and of the direction that do not
 // involve alpha: L = ln u1 + cos^2(2 pi u2) ln u3 (X = -L / alpha), u4^2,
 // and cos(theta), sin(theta), cos(phi), sin(phi).  cm_update_f computes
-// them for all three subgroups before the sequential part, as six
+// them for all three subgroups before the sequential part, as five
 // independent Philox chains that the scheduler can interleave; each
 // subgroup then runs only the alpha-dependent steps.  The arithmetic and its
 // order are those of su2_draw_f<false>; rejected first proposals (further
@@ -787,8 +798,7 @@ struct DrawPre {
   float L, u4sq, costh, sinth, cphi, sphi;
 };
 
-__device__ __forceinline__ DrawPre draw_pre_f(uint2 key, uint32_t c0, uint32_t c1, uint32_t tag) {
-  DrawPre p;
+__device__ __forceinline__ void proposal_pre_f(DrawPre &p, uint2 key, uint32_t c0, uint32_t c1, uint32_t tag) {
   const uint4 w = philox4x32_10(make_uint4(c0, c1, tag, kPurposeHeatbath), key);
   const float ang = __fmaf_rn(unif_f(w.y), 6.28318530717958648f, -3.14159265358979324f);
   const float cs = __cosf(ang);
@@ -797,14 +807,16 @@ __device__ __forceinline__ DrawPre draw_pre_f(uint2 key, uint32_t c0, uint32_t c
   p.L = l1 + cs * cs * l3;
   const float u4 = unif_f(w.w);
   p.u4sq = u4 * u4;
-  const uint4 v = philox4x32_10(make_uint4(c0, c1, tag | kHitDirection, kPurposeHeatbath), key);
-  p.costh = 2.0f * unif_f(v.x) - 1.0f;
+}
+
+// The direction from its two words (those direction_words returns).
+__device__ __forceinline__ void direction_pre_f(DrawPre &p, uint32_t wx, uint32_t wy) {
+  p.costh = 2.0f * unif_f(wx) - 1.0f;
   p.sinth = sqrt_sfu(1.0f - p.costh * p.costh);
   float sphi, cphi;
-  __sincosf(__fmaf_rn(unif_f(v.y), 6.28318530717958648f, -3.14159265358979324f), &sphi, &cphi);
+  __sincosf(__fmaf_rn(unif_f(wy), 6.28318530717958648f, -3.14159265358979324f), &sphi, &cphi);
   p.sphi = -sphi;  // sin(2 pi u) = -sin(2 pi (u - 1/2)), likewise cos
   p.cphi = -cphi;
-  return p;
 }
 
 // The float draw of one subgroup from its precomputed first proposal.
@@ -841,7 +853,13 @@ __device__ __forceinline__ void cm_update_f(M3<float> &U, const M3<float> &A, fl
                                             uint32_t &nacc, float &dretr) {
   DrawPre pre[3];
 #pragma unroll
-  for (int sg = 0; sg < 3; ++sg) pre[sg] = draw_pre_f(key, c0, c1, heatbath_tag(colour, mu, sg));
+  for (int sg = 0; sg < 3; ++sg) proposal_pre_f(pre[sg], key, c0, c1, heatbath_tag(colour, mu, sg));
+  // the two direction blocks, split as direction_words splits them
+  const uint4 d01 = philox4x32_10(make_uint4(c0, c1, heatbath_tag(colour, mu, 0) | kHitDirection, kPurposeHeatbath), key);
+  const uint4 d2 = philox4x32_10(make_uint4(c0, c1, heatbath_tag(colour, mu, 2) | kHitDirection, kPurposeHeatbath), key);
+  direction_pre_f(pre[0], d01.x, d01.y);
+  direction_pre_f(pre[1], d01.z, d01.w);
+  direction_pre_f(pre[2], d2.x, d2.y);
   dretr = 0.0f;
   const float ca = 2.0f * beta / 3.0f;
 #pragma unroll

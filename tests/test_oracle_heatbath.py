@@ -34,8 +34,9 @@ def test_su2_one_hit_acceptance(alpha):
     assert abs(acc.mean() - p) < 5 * err
 
 
-def test_su2_draw_is_unit_and_isotropic():
-    x, acc = oracle.su2_samples(3.0, hits=50, seed=2, n=100_000)
+@pytest.mark.parametrize("subgroup", [0, 1, 2])
+def test_su2_draw_is_unit_and_isotropic(subgroup):
+    x, acc = oracle.su2_samples(3.0, hits=50, seed=2, n=100_000, subgroup=subgroup)
     x = x[acc]
     np.testing.assert_allclose(np.sum(x * x, axis=1), 1.0, atol=1e-14)
     # the vector part points uniformly on the sphere: mean 0, equal second moments
@@ -44,6 +45,25 @@ def test_su2_draw_is_unit_and_isotropic():
     m2 = (v ** 2).mean(axis=0)
     target = (1 - x[:, 0] ** 2).mean() / 3
     assert np.all(np.abs(m2 - target) < 0.01 * target + 5 * (v ** 2).std(axis=0) / np.sqrt(len(v)))
+
+
+def test_su2_directions_of_the_three_subgroups_are_independent():
+    """The three subgroups of one link update draw their directions from two
+    random-number blocks (two words each; subgroups 0 and 1 share a block).
+    At the same counter the three unit directions must be uncorrelated: a
+    subgroup reading another one's words would repeat its direction."""
+    n = 50_000
+    dirs = []
+    for sg in range(3):
+        x, acc = oracle.su2_samples(3.0, hits=50, seed=4, n=n, subgroup=sg)
+        assert acc.all()
+        v = x[:, 1:]
+        dirs.append(v / np.linalg.norm(v, axis=1, keepdims=True))
+    for a, b in [(0, 1), (0, 2), (1, 2)]:
+        dot = np.sum(dirs[a] * dirs[b], axis=1)  # 1/3 variance for independent isotropic directions
+        assert abs(dot.mean()) < 5 * np.sqrt(1 / 3 / n)
+        cos_theta = dirs[a][:, 2] * dirs[b][:, 2]
+        assert abs(cos_theta.mean()) < 5 * np.sqrt(1 / 9 / n)
 
 
 def _random_su3(rng):

@@ -33,7 +33,9 @@ MUTATIONS = {
     "kp_dropped_cos2": ("X = -(log(u[0]) + c * c * log(u[2])) / alpha;", "X = -(log(u[0]) + log(u[2])) / alpha;"),
     "kp_accept_not_squared": ("double lhs = u[3] * u[3], rhs", "double lhs = u[3], rhs"),
     "direction_radius": ("double rho = sqrt(X * (2.0 - X));", "double rho = sqrt(X * (1.0 - X));"),
-    "direction_not_isotropic": ("double costh = 2.0 * u[0] - 1.0;", "double costh = u[0];"),
+    "direction_not_isotropic": ("double costh = 2.0 * u5 - 1.0;", "double costh = u5;"),
+    "direction_words_repeated": ("double u5 = subgroup == 1 ? u[2] : u[0], u6 = subgroup == 1 ? u[3] : u[1];",
+                                 "double u5 = u[0], u6 = u[1];"),
     "plaquette_missing_dagger": ("mat3 c = link_at(g, U, ln, sn, mu); c = m_dag(&c);\n  mat3 d",
                                  "mat3 c = link_at(g, U, ln, sn, mu);\n  mat3 d"),
     "plaquette_time_split": ("if (nu == D - 1) { sum_t", "if (mu == 0) { sum_t"),
@@ -83,6 +85,11 @@ def check_su2():
     _, acc1 = oracle.su2_samples(4.0, 1, 2, 60_000)
     p = exact.kp_acceptance(4.0)
     assert abs(acc1.mean() - p) < 5 * np.sqrt(p * (1 - p) / len(acc1))
+    # the subgroups' directions at one counter are independent
+    v = [oracle.su2_samples(3.0, 50, 4, 20_000, subgroup=sg)[0][:, 1:] for sg in range(3)]
+    v = [w / np.linalg.norm(w, axis=1, keepdims=True) for w in v]
+    for a, b in [(0, 1), (0, 2), (1, 2)]:
+        assert abs(np.sum(v[a] * v[b], axis=1).mean()) < 5 * np.sqrt(1 / 3 / 20_000)
 
 
 def check_frozen_staple():
