@@ -217,21 +217,27 @@ def graph_stage_times(su3, torch, stream, seed, step_ms):
     + 1 re-unitarisation per 10-sweep call (T10), one re-unitarised every 20
     sweeps 160 + 1 per 20-sweep call (T20); neither measures.  Then
     update tick = (T20 - T10) / 80, re-unitarisation = T10 - 80 x tick (it
-    carries the call's one-block arm kernel), measurement = step - T10."""
+    carries the call's one-block arm kernel), measurement = step - T10.
+    T10 and T20 are each the fastest of three alternating timings: a single
+    pair moved the derived tick by ~1 us between runs."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    per_call = {}
-    for every, calls in ((10, 12), (20, 6)):
-        lat = su3.Lattice(DIMS, beta=BETA, seed=seed, hits=HITS, storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT,
-                          reunit_every=every, stream=stream)
-        lat.autotune()
-        lat.sweep(every)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(calls):
-            lat.sweep(every)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        per_call[every] = e0.elapsed_time(e1) / calls
+    lats = {}
+    for every in (10, 20):
+        lats[every] = su3.Lattice(DIMS, beta=BETA, seed=seed, hits=HITS, storage=su3.SU3_FP32_12,
+                                  start=su3.SU3_START_HOT, reunit_every=every, stream=stream)
+        lats[every].autotune()
+        lats[every].sweep(every)
+    per_call = {10: float("inf"), 20: float("inf")}
+    for _ in range(3):
+        for every, calls in ((10, 12), (20, 6)):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(calls):
+                lats[every].sweep(every)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per_call[every] = min(per_call[every], e0.elapsed_time(e1) / calls)
+    for lat in lats.values():
         lat.close()
     ticks = 2 * len(DIMS) * SWEEPS_PER_STEP
     tick_ms = (per_call[20] - per_call[10]) / ticks

@@ -441,9 +441,10 @@ struct Engine {
   std::vector<Chain> chains;
   // device mirrors
   ChainDesc *d_desc = nullptr;
-  ChainState *d_state = nullptr;
+  ChainState *d_state = nullptr;  // [chain][2]: the slot EngineHeader::parity is current
   EngineHeader *d_hdr = nullptr;
   int32_t *d_tile_chain = nullptr;
+  int32_t *d_meas_list = nullptr;  // [chain_cap] the chains a launch measures
   size_t tile_cap = 0, chain_cap = 0;
   double *d_meas_out = nullptr;  // stand-alone measurement results
   double *h_pinned = nullptr;    // small pinned staging (results, counters)
@@ -554,10 +555,12 @@ struct Engine {
     cudaFree(d_state);
     cudaFree(d_hdr);
     cudaFree(d_tile_chain);
+    cudaFree(d_meas_list);
     cudaFree(d_meas_out);
     cudaFreeHost(h_pinned);
     d_desc = nullptr;
     d_state = nullptr;
+    d_meas_list = nullptr;
     d_hdr = nullptr;
     d_tile_chain = nullptr;
     d_meas_out = nullptr;
@@ -695,7 +698,7 @@ struct Engine {
       ChainState *ds = nullptr;
       CU(cudaMallocAsync(&ds, sizeof(ChainState), stream));
       CU(cudaMemsetAsync(ds, 0, sizeof(ChainState), stream));
-      CU(launch_halo(storage, dd, ds, 1, ch.desc.nlayers * ch.desc.nb, ch.halo_n[0] + ch.halo_n[1], stream));
+      CU(launch_halo(storage, dd, ds, nullptr, 1, ch.desc.nlayers * ch.desc.nb, ch.halo_n[0] + ch.halo_n[1], stream));
       CU(cudaFreeAsync(ds, stream));
     } else {
       CU(launch_start(storage, dd, nlinks, ch.cfg.start == SU3_START_HOT, stream));
@@ -737,9 +740,12 @@ struct Engine {
     if (chains.size() > chain_cap) {
       cudaFree(d_desc);
       cudaFree(d_state);
+      cudaFree(d_meas_list);
+      d_meas_list = nullptr;
       chain_cap = std::max<size_t>(chains.size(), 2 * chain_cap);
       CU(cudaMalloc(&d_desc, chain_cap * sizeof(ChainDesc)));
-      CU(cudaMalloc(&d_state, chain_cap * sizeof(ChainState)));
+      CU(cudaMalloc(&d_state, 2 * chain_cap * sizeof(ChainState)));
+      CU(cudaMalloc(&d_meas_list, chain_cap * sizeof(int32_t)));
       drop_graph();
     }
     if ((size_t)tiles > tile_cap) {
@@ -750,18 +756,20 @@ struct Engine {
     }
     std::vector<int32_t> map(tiles);
     std::vector<ChainDesc> descs(chains.size());
-    std::vector<ChainState> states(chains.size());
+    std::vector<ChainState> states(2 * chains.size());
     for (size_t c = 0; c < chains.size(); ++c) {
       const ChainDesc &d = chains[c].desc;
       for (int t = 0; t < d.nlayers * d.tiles_per_layer; ++t) map[d.tile_base + t] = (int32_t)c;
       descs[c] = d;
-      states[c] = chains[c].state;
+      states[2 * c] = states[2 * c + 1] = chains[c].state;
     }
     EngineHeader h{};
     h.nchains = (int32_t)chains.size();
     h.total_tiles = tiles;
     h.tile = block;
-    h.done_warps = 0;
+    h.parity = 0;
+    h.done = 0;
+    h.n_meas = 0;
     // Pageable copies are staged by the driver before the call returns.
     if (tiles) CU(cudaMemcpyAsync(d_tile_chain, map.data(), tiles * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
     if (!chains.empty()) {
@@ -774,21 +782,27 @@ struct Engine {
     return SU3_OK;
   }
 
+  // Both state slots of every chain get the host mirror's state, so the
+  // parity does not matter.
   su3_status upload_states() {
-    std::vector<ChainState> states(chains.size());
-    for (size_t c = 0; c < chains.size(); ++c) states[c] = chains[c].state;
+    std::vector<ChainState> states(2 * chains.size());
+    for (size_t c = 0; c < chains.size(); ++c) states[2 * c] = states[2 * c + 1] = chains[c].state;
     if (!states.empty())
       CU(cudaMemcpyAsync(d_state, states.data(), states.size() * sizeof(ChainState), cudaMemcpyHostToDevice, stream));
     CU(cudaStreamSynchronize(stream));
     return SU3_OK;
   }
 
+  // The current slot of every chain (EngineHeader::parity).
   su3_status download_states() {
-    std::vector<ChainState> states(chains.size());
+    std::vector<ChainState> states(2 * chains.size());
+    EngineHeader h{};
     if (!states.empty())
       CU(cudaMemcpyAsync(states.data(), d_state, states.size() * sizeof(ChainState), cudaMemcpyDeviceToHost, stream));
+    CU(cudaMemcpyAsync(&h, d_hdr, sizeof h, cudaMemcpyDeviceToHost, stream));
     CU(cudaStreamSynchronize(stream));
-    for (size_t c = 0; c < chains.size(); ++c) chains[c].state = states[c];
+    const int p = h.parity & 1;
+    for (size_t c = 0; c < chains.size(); ++c) chains[c].state = states[2 * c + p];
     return SU3_OK;
   }
 
@@ -817,12 +831,12 @@ struct Engine {
     return SU3_OK;
   }
 
-  EngineArgs args() const { return EngineArgs{d_desc, d_state, d_hdr, d_tile_chain}; }
+  EngineArgs args() const { return EngineArgs{d_desc, d_state, d_hdr, d_tile_chain, d_meas_list}; }
 
   // Halo refresh of the (only) chain of an engine with a divided chain.
   cudaError_t halo_refresh(ChainDesc *dd, ChainState *ds, int all) const {
     const Chain &ch = chains[0];
-    return launch_halo(storage, dd, ds, all, ch.desc.nlayers * ch.desc.nb, ch.halo_n[0] + ch.halo_n[1], stream);
+    return launch_halo(storage, dd, ds, d_hdr, all, ch.desc.nlayers * ch.desc.nb, ch.halo_n[0] + ch.halo_n[1], stream);
   }
 
   // One tick, and for a divided chain the halo refresh of what it changed.
@@ -845,7 +859,7 @@ struct Engine {
     Chain &ch = chains[c];
     const size_t nlinks = (size_t)ch.desc.nlayers * ch.desc.D * ch.desc.V;
     CU(launch_sub_copy(storage, d_desc + c, ch.d_pdesc, nlinks, to_sub, stream));
-    if (to_sub) CU(halo_refresh(d_desc + c, d_state + c, 1));
+    if (to_sub) CU(halo_refresh(d_desc + c, d_state + 2 * c, 1));
     return SU3_OK;
   }
 
@@ -1042,7 +1056,7 @@ struct Engine {
   su3_status action_reset(size_t c) {
     Chain &ch = chains[c];
     if (ch.state.anchor) {  // restarting now: no restart at the next measurement
-      CU(launch_set_anchor(d_state + c, 0, stream));
+      CU(launch_set_anchor(d_state + 2 * c, 0, stream));
       ch.state.anchor = 0;
     }
     CU(cudaMemsetAsync(ch.action_slots, 0, (size_t)ch.n_action_slots * sizeof(double), stream));
@@ -1062,7 +1076,7 @@ struct Engine {
   su3_status action_defer(size_t c) {
     Chain &ch = chains[c];
     if (ch.desc.weighted || ch.desc.measure_every <= 0) return action_reset(c);
-    CU(launch_set_anchor(d_state + c, 1, stream));
+    CU(launch_set_anchor(d_state + 2 * c, 1, stream));
     ch.state.anchor = 1;
     return SU3_OK;
   }

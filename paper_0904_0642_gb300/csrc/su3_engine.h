@@ -4,9 +4,13 @@
 // the tick kernel moves every active chain one stage forward: one
 // (colour, direction) phase of the checkerboard sweep, or a
 // re-unitarisation, or a measurement.  The stage machine lives in device
-// memory and is advanced by the last CTA of each launch, so a captured graph
-// of ticks replays without host involvement and chains of different D can
-// share a launch.
+// memory, so a captured graph of ticks replays without host involvement and
+// chains of different D can share a launch.  Every chain has two state
+// slots, and a launch reads slot `parity`.  With several chains, the first
+// warp of a launch to finish writes every chain's next state into the other
+// slot while the rest of the launch runs, and the last one finishes the
+// tick's measurements and flips the parity; a single chain is advanced in
+// place by the launch's last warp.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -108,14 +112,18 @@ struct EngineHeader {
   int32_t nchains;
   int32_t total_tiles;
   int32_t tile;            // threads per CTA = sites per tile
-  uint32_t done_warps;     // last-warp detection (the last warp to finish runs the stage machines)
+  int32_t parity;          // the state slot that holds every chain's current state
+  uint32_t done;           // warps counted (bits 0-30); bit 31: some chain measures in this tick
+  int32_t n_meas;          // chains entered in meas_list by this launch
+  int32_t pad[2];
 };
 
 struct EngineArgs {
   ChainDesc *desc;
-  ChainState *state;
+  ChainState *state;       // [chain][2]: slot parity current, the other one next
   EngineHeader *hdr;
   int32_t *tile_chain;     // [total_tiles] -> chain
+  int32_t *meas_list;      // [chains] chains whose measurement the last warp finishes
 };
 
 }  // namespace su3g

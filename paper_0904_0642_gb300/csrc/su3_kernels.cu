@@ -4,8 +4,10 @@
 //   (a (colour, direction) update phase, a re-unitarisation or a
 //   measurement).  One thread per site of the tile (tile = CTA width); tiles
 //   of all chains are spread over a grid of CTAs sized to the SM count.
-//   The last CTA to finish advances each chain's stage machine and reduces
-//   measurement partial sums in a fixed order.
+//   The chains' stage machines advance at the end of the launch (one
+//   chain: by the last warp to finish; several: by the first, into a second
+//   state slot, with the last one flipping the slot parity), and the last
+//   warp reduces measurement partial sums in a fixed order.
 // k_start, k_convert, k_measure*: start configurations, canonical-layout
 //   conversion and stand-alone measurements.
 #include <cstdio>
@@ -683,13 +685,23 @@ __device__ __forceinline__ void restart_bookkeeping(const ChainDesc &d, const do
 
 // ------------------------------------------------------------------ tick kernel
 
-__device__ __forceinline__ void load_chain(const EngineArgs &ea, int c, ChainDesc &sd, ChainState &ss) {
+// Copy a chain's descriptor and its current state (of its two state slots,
+// the one the launch's parity names; the parity is the same for the whole
+// launch) into the CTA's shared memory.  Both slots and the parity are
+// loaded together and the current one selected, so that no load waits for
+// another.
+__device__ __forceinline__ void load_chain(const EngineArgs &ea, int c, ChainDesc &sd, ChainState &ss, int &s_par) {
   const int n1 = sizeof(ChainDesc) / 4, n2 = sizeof(ChainState) / 4;
   const uint32_t *src1 = reinterpret_cast<const uint32_t *>(ea.desc + c);
-  const uint32_t *src2 = reinterpret_cast<const uint32_t *>(ea.state + c);
+  const uint32_t *src2 = reinterpret_cast<const uint32_t *>(ea.state + 2 * (size_t)c);
   uint32_t *dst1 = reinterpret_cast<uint32_t *>(&sd), *dst2 = reinterpret_cast<uint32_t *>(&ss);
   for (int i = threadIdx.x; i < n1; i += blockDim.x) dst1[i] = src1[i];
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) dst2[i] = __ldcg(src2 + i);
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    const uint32_t w0 = __ldcg(src2 + i), w1 = __ldcg(src2 + n2 + i);
+    const int par = __ldcg(&ea.hdr->parity);
+    dst2[i] = par ? w1 : w0;
+    if (i == 0) s_par = par;
+  }
 }
 
 // Warp-sum the FHKP counters and add them to the chain's totals.
@@ -738,6 +750,22 @@ __device__ __host__ inline void advance_stage(const ChainDesc &d, ChainState &s)
   advance_stage(StageParams{d.D, d.reunit_every, d.measure_every}, s);
 }
 
+// The state of a chain after this launch's tick.
+__device__ __forceinline__ ChainState next_state(const StageParams &p, ChainState s) {
+  if (!s.active) {
+    s.prev_stage = -1;  // nothing ran: no halo refresh
+    return s;
+  }
+  if (s.stage == kStageMeasure) {
+    s.n_meas += 1;
+    s.anchor = 0;  // the measurement restarts the bookkeeping if it was set
+  }
+  advance_stage(p, s);
+  return s;
+}
+
+__device__ __forceinline__ bool measures(const ChainState &s) { return s.active && s.stage == kStageMeasure; }
+
 // Register variants of the tick kernel: __launch_bounds__(threads, CTAs per
 // SM) caps registers at 65536 / (threads x CTAs).  The autotuner times them.
 // kRolled: the update keeps its loop over staple directions rolled.
@@ -766,7 +794,8 @@ template <> struct TickBounds<10> { static constexpr int kThreads = 256, kMinBlo
 template <class S, int V, bool WT, bool SUB = false, bool TOR = false>
 __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBlocks) k_tick(EngineArgs ea) {
   __shared__ ChainDesc sd;
-  __shared__ ChainState ss;
+  __shared__ ChainState ss;  // the current chain's current state
+  __shared__ int s_par;      // the state slot that holds the current states
   __shared__ double s_red[32 * kPartVals];
   // Launched as a programmatic dependent (pdl), this tick may be scheduled
   // before the previous kernel of the stream has finished: wait for its
@@ -784,7 +813,7 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
     if (c != cur) {
       if (cur >= 0) flush_counters(sd, np, na);
       __syncthreads();  // every warp is done with the previous descriptor
-      load_chain(ea, c, sd, ss);
+      load_chain(ea, c, sd, ss, s_par);
       __syncthreads();
       cur = c;
     }
@@ -828,100 +857,107 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
     }
   }
   if (cur >= 0) flush_counters(sd, np, na);
-  // The last warp of the grid to finish advances the stage machines and
-  // finishes measurements.  Counting warps, not CTAs, lets a warp leave as
-  // soon as its own work is done (no CTA-wide barrier at the end).  Only the
-  // measurement partials are read by the last warp, so only their writers
+  // The end of the launch's stage machine.  Counting warps, not CTAs, lets a
+  // warp leave as soon as its own work is done (no CTA-wide barrier at the
+  // end).  Writers of what a later warp of this launch reads (measurement
+  // partials; with several chains also next states and the measuring list)
   // fence before counting (release); link stores and counter adds are
   // ordered for the next launch by the launch boundary.
+  // One chain: the last warp to finish advances it in place, from its CTA's
+  // shared copies (no global reads); the parity stays.
+  // Several chains: the first warp to finish writes every chain's next state
+  // into the chain's other state slot (the current slot is only read during
+  // a launch, so this overlaps the tiles still running) and lists the chains
+  // that measure in this tick; then it counts itself a second time.  The
+  // warp whose count completes the grid's warps + 1 finishes those
+  // measurements and flips the parity.  (Reading and advancing hundreds of
+  // chain states at the end of the launch, by the last warp, had kept the
+  // rest of the GPU idle for several microseconds per tick.)
   const int lane = threadIdx.x & 31;
-  unsigned prev = 0;
+  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+  constexpr uint32_t kMeasFlag = 0x80000000u;
+  uint32_t prev = 0;
   if (lane == 0) {
     if (wrote_partials) __threadfence();
-    prev = atomicAdd(&ea.hdr->done_warps, 1u);
+    prev = atomicAdd(&ea.hdr->done, 1u);
   }
   prev = __shfl_sync(0xffffffffu, prev, 0);
-  if (prev != gridDim.x * (blockDim.x >> 5) - 1) return;
+  const int par = cur >= 0 ? s_par : __ldcg(&ea.hdr->parity);
   if (nchains == 1 && cur == 0) {
-    // One chain, whose state and descriptor this CTA holds: no global reads
-    // and, outside measurement ticks, no fence (the next launch orders the
-    // state write).
-    ChainState st = ss;
-    if (st.active) {
-      if (st.stage == kStageMeasure) {
-        __threadfence();  // acquire the partials of every tile
-        double *out = sd.results + (size_t)(st.n_meas % (uint32_t)sd.result_cap) * (sd.nlayers + 1) * kMeasVals;
-        finalize_measure(sd, sd.partials, out);
-        if (st.anchor) {
-          restart_bookkeeping(sd, out);
-          st.anchor = 0;
-        }
-        st.n_meas += 1;
-      }
-      advance_stage(StageParams{sd.D, sd.reunit_every, sd.measure_every}, st);
-    } else {
-      st.prev_stage = -1;  // nothing ran: no halo refresh
+    if (prev != nwarps - 1) return;
+    if (measures(ss)) {
+      __threadfence();  // acquire the partials of every tile
+      double *out = sd.results + (size_t)(ss.n_meas % (uint32_t)sd.result_cap) * (sd.nlayers + 1) * kMeasVals;
+      finalize_measure(sd, sd.partials, out);
+      if (ss.anchor) restart_bookkeeping(sd, out);
     }
+    const ChainState st = next_state(StageParams{sd.D, sd.reunit_every, sd.measure_every}, ss);
     if (lane == 0) {
-      ea.state[0] = st;
-      ea.hdr->done_warps = 0;
+      ea.state[par] = st;  // every other warp has read it
+      ea.hdr->done = 0u;
     }
     return;
   }
-  // Every chain's state is read once (four per lane in flight, so that
-  // their loads overlap; the previous launch ordered them), chains in a
-  // measurement stage are finished by the whole warp, then every state is
-  // advanced and written.  A fence (acquiring the tiles' partials) only
-  // when some chain measures.
-  constexpr int kU = 4;
-  bool fenced = false;
-  for (int base = 0; base < nchains; base += 32 * kU) {
-    ChainState st[kU];
-    StageParams sp[kU];
+  int nmeas = -1;  // known to the first warp; the others read it when flagged
+  if (prev == 0) {
+    nmeas = 0;
+    {
+      // every chain's state read once, four per lane in flight; the
+      // measuring chains listed in chain order (ballot prefix)
+      constexpr int kU = 4;
+      for (int base = 0; base < nchains; base += 32 * kU) {
+        ChainState st[kU];
+        StageParams sp[kU];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int c = base + 32 * u + lane;
-      if (c < nchains) {
-        st[u] = ea.state[c];
-        const ChainDesc &d = ea.desc[c];
-        sp[u] = StageParams{d.D, d.reunit_every, d.measure_every};
+        for (int u = 0; u < kU; ++u) {
+          const int c = base + 32 * u + lane;
+          if (c < nchains) {
+            st[u] = ea.state[2 * (size_t)c + par];
+            const ChainDesc &d = ea.desc[c];
+            sp[u] = StageParams{d.D, d.reunit_every, d.measure_every};
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int c = base + 32 * u + lane;
+          const bool m = c < nchains && measures(st[u]);
+          const unsigned mask = __ballot_sync(0xffffffffu, m);
+          if (m) {
+            const int slot = nmeas + __popc(mask & ((1u << lane) - 1u));
+            if (in_bounds(slot, nchains, kBoundsSlot)) ea.meas_list[slot] = c;
+          }
+          nmeas += __popc(mask);
+          if (c < nchains) ea.state[2 * (size_t)c + (par ^ 1)] = next_state(sp[u], st[u]);
+        }
       }
     }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int c = base + 32 * u + lane;
-      const bool meas = c < nchains && st[u].active && st[u].stage == kStageMeasure;
-      unsigned todo = __ballot_sync(0xffffffffu, meas);
-      if (todo && !fenced) {
-        __threadfence();
-        fenced = true;
-      }
-      while (todo) {
-        const int k = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const uint32_t n_meas = __shfl_sync(0xffffffffu, st[u].n_meas, k);
-        const int anchor = __shfl_sync(0xffffffffu, st[u].anchor, k);
-        const ChainDesc &d = ea.desc[base + 32 * u + k];
-        double *out = d.results + (size_t)(n_meas % (uint32_t)d.result_cap) * (d.nlayers + 1) * kMeasVals;
-        finalize_measure(d, d.partials, out);
-        if (anchor) restart_bookkeeping(d, out);
-      }
-      if (meas) st[u].anchor = 0;
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int c = base + 32 * u + lane;
-      if (c >= nchains) continue;
-      if (!st[u].active) {
-        if (st[u].prev_stage != -1) ea.state[c].prev_stage = -1;  // nothing ran: no halo refresh
-        continue;
-      }
-      if (st[u].stage == kStageMeasure) st[u].n_meas += 1;
-      advance_stage(sp[u], st[u]);
-      ea.state[c] = st[u];
+    if (lane == 0) ea.hdr->n_meas = nmeas;
+    __threadfence();  // each lane's next states and list entries before the count
+    __syncwarp();
+    if (lane == 0) prev = atomicAdd(&ea.hdr->done, 1u | (nmeas ? kMeasFlag : 0u));
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+  }
+  if ((prev & ~kMeasFlag) != nwarps) return;
+  // The last count: finish the listed measurements, flip the parity.
+  if (nmeas < 0) nmeas = (prev & kMeasFlag) ? -2 : 0;
+  if (nmeas != 0) {
+    __threadfence();  // acquire the tiles' partials, the list and its length
+    if (nmeas < 0) nmeas = __ldcg(&ea.hdr->n_meas);
+    for (int i = 0; i < nmeas && i < nchains; ++i) {
+      const int c = __ldcg(ea.meas_list + i);
+      if (!in_bounds(c, nchains, kBoundsSlot)) continue;
+      const ChainDesc &d = ea.desc[c];
+      // the current slot: this tick's measurement count and anchor
+      const ChainState &s = ea.state[2 * (size_t)c + par];
+      double *out = d.results + (size_t)(s.n_meas % (uint32_t)d.result_cap) * (d.nlayers + 1) * kMeasVals;
+      finalize_measure(d, d.partials, out);
+      if (s.anchor) restart_bookkeeping(d, out);
     }
   }
-  if (lane == 0) ea.hdr->done_warps = 0;
+  if (lane == 0) {
+    ea.hdr->parity = par ^ 1;
+    ea.hdr->done = 0u;
+  }
 }
 
 // ------------------------------------------------------------------ stand-alone measurement
@@ -968,17 +1004,24 @@ __global__ void k_action_sum(const double *slots, int n, double *out) {
 
 // Arm every chain of an engine for n more sweeps, in stream order (the host
 // mirror does the same): no host buffer, so nothing to synchronise on.
+// Both state slots of a chain hold its current state between launches
+// as far as the host-visible fields go: arm them both (the next launch
+// overwrites the one that is not current).
 __global__ void k_arm(ChainState *state, int nchains, uint32_t n) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nchains; c += gridDim.x * blockDim.x) {
-    ChainState s = state[c];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * nchains; i += gridDim.x * blockDim.x) {
+    ChainState s = state[i];
     s.target = s.sweep + n;
     s.active = 1;
-    state[c] = s;
+    state[i] = s;
   }
 }
 
-// Set the bookkeeping-restart flag of one chain, in stream order.
-__global__ void k_set_anchor(ChainState *state, int value) { state->anchor = value; }
+// Set the bookkeeping-restart flag of one chain (both state slots), in
+// stream order.
+__global__ void k_set_anchor(ChainState *state, int value) {
+  state[0].anchor = value;
+  state[1].anchor = value;
+}
 
 cudaError_t launch_set_anchor(ChainState *state, int value, cudaStream_t st) {
   k_set_anchor<<<1, 1, 0, st>>>(state, value);
@@ -1098,11 +1141,11 @@ __global__ void k_convert(ChainDesc *desc_dev, double *canon, int to_canonical) 
 // code, whose box coordinate wraps periodically; a wrap across a glued
 // boundary of the double-layered torus lands in the other layer.
 template <class S>
-__global__ void k_halo(const ChainDesc *desc_dev, const ChainState *state_dev, int all) {
+__global__ void k_halo(const ChainDesc *desc_dev, const ChainState *state_dev, const EngineHeader *hdr, int all) {
   const ChainDesc &d = *desc_dev;
   int c0 = 0, c1 = 2, m0 = 0, m1 = d.D;
   if (!all) {
-    const int ps = state_dev->prev_stage;
+    const int ps = state_dev[hdr->parity].prev_stage;  // the chain's current state slot
     if (ps >= 0 && ps < 2 * d.D) {
       c0 = ps / d.D;
       c1 = c0 + 1;
@@ -1445,13 +1488,13 @@ cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, bool 
                   : tick_dispatch<TickLaunch, false>(storage, variant, sub, torus, pa, grid, block, st, pdl);
 }
 
-cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, int all, int boxes,
-                        int halo_sites, cudaStream_t st) {
+cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, const EngineHeader *hdr,
+                        int all, int boxes, int halo_sites, cudaStream_t st) {
   const int block = 256;
   const dim3 grid((unsigned)((halo_sites + block - 1) / block > 0 ? (halo_sites + block - 1) / block : 1),
                   (unsigned)boxes);
   return by_storage(storage, [&](auto s) {
-    k_halo<decltype(s)><<<grid, block, 0, st>>>(desc_dev, state_dev, all);
+    k_halo<decltype(s)><<<grid, block, 0, st>>>(desc_dev, state_dev, hdr, all);
     return cudaGetLastError();
   });
 }

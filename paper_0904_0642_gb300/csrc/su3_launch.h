@@ -23,8 +23,8 @@ cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, bool 
 // Halo refresh of a divided chain (after its tick, or all links), and the
 // copies between its sublattice boxes and the undivided layout.
 // boxes: layers x sublattices; halo_sites: halo sites of one box (both colours).
-cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, int all, int boxes,
-                        int halo_sites, cudaStream_t st);
+cudaError_t launch_halo(int storage, const ChainDesc *desc_dev, const ChainState *state_dev, const EngineHeader *hdr,
+                        int all, int boxes, int halo_sites, cudaStream_t st);
 cudaError_t launch_sub_copy(int storage, const ChainDesc *sub_dev, const ChainDesc *plain_dev, size_t nlinks,
                             int to_sub, cudaStream_t st);
 cudaError_t launch_measure(int storage, ChainDesc *desc_dev, int tiles_total, int block, double *out, cudaStream_t st);
