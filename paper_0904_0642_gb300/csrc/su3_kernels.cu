@@ -766,6 +766,23 @@ __device__ __forceinline__ ChainState next_state(const StageParams &p, ChainStat
 
 __device__ __forceinline__ bool measures(const ChainState &s) { return s.active && s.stage == kStageMeasure; }
 
+// The end of a one-chain launch, by its last warp: finish the measurement
+// and advance the chain's state in place (every other warp has read it).
+__device__ __forceinline__ void finish_single_chain(const EngineArgs &ea, const ChainDesc &d, const ChainState &cs,
+                                                    int par, int lane) {
+  if (measures(cs)) {
+    __threadfence();  // acquire the partials of every tile
+    double *out = d.results + (size_t)(cs.n_meas % (uint32_t)d.result_cap) * (d.nlayers + 1) * kMeasVals;
+    finalize_measure(d, d.partials, out);
+    if (cs.anchor) restart_bookkeeping(d, out);
+  }
+  const ChainState st = next_state(StageParams{d.D, d.reunit_every, d.measure_every}, cs);
+  if (lane == 0) {
+    ea.state[par] = st;
+    ea.hdr->done = 0u;
+  }
+}
+
 // Register variants of the tick kernel: __launch_bounds__(threads, CTAs per
 // SM) caps registers at 65536 / (threads x CTAs).  The autotuner times them.
 // kRolled: the update keeps its loop over staple directions rolled.
@@ -864,7 +881,9 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
   // fence before counting (release); link stores and counter adds are
   // ordered for the next launch by the launch boundary.
   // One chain: the last warp to finish advances it in place, from its CTA's
-  // shared copies (no global reads); the parity stays.
+  // shared copies (no global reads); the parity stays.  Every warp of a
+  // one-chain launch takes this path, so that exactly one count per warp
+  // is made.
   // Several chains: the first warp to finish writes every chain's next state
   // into the chain's other state slot (the current slot is only read during
   // a launch, so this overlaps the tiles still running) and lists the chains
@@ -883,19 +902,14 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
   }
   prev = __shfl_sync(0xffffffffu, prev, 0);
   const int par = cur >= 0 ? s_par : __ldcg(&ea.hdr->parity);
-  if (nchains == 1 && cur == 0) {
+  if (nchains == 1) {
     if (prev != nwarps - 1) return;
-    if (measures(ss)) {
-      __threadfence();  // acquire the partials of every tile
-      double *out = sd.results + (size_t)(ss.n_meas % (uint32_t)sd.result_cap) * (sd.nlayers + 1) * kMeasVals;
-      finalize_measure(sd, sd.partials, out);
-      if (ss.anchor) restart_bookkeeping(sd, out);
-    }
-    const ChainState st = next_state(StageParams{sd.D, sd.reunit_every, sd.measure_every}, ss);
-    if (lane == 0) {
-      ea.state[par] = st;  // every other warp has read it
-      ea.hdr->done = 0u;
-    }
+    // (a CTA of a grid captured for more tiles than the engine now has can
+    // have run no tile: it reads the chain from global memory)
+    if (cur == 0)
+      finish_single_chain(ea, sd, ss, par, lane);
+    else
+      finish_single_chain(ea, ea.desc[0], ea.state[par], par, lane);
     return;
   }
   int nmeas = -1;  // known to the first warp; the others read it when flagged

@@ -55,6 +55,28 @@ def test_jobs_in_the_mix_equal_jobs_alone():
         assert r.submit_s <= r.start_s <= r.finish_s
 
 
+def test_job_alone_on_a_grid_captured_for_more_tiles():
+    """The worker keeps its captured graph of ticks across admissions and
+    retirements, so a job that outlives a larger one runs alone on a grid
+    sized for more tiles: some CTAs run no tile.  The job must finish and
+    equal the same job run alone."""
+    big = (0, [8, 8, 8, 8], su3.SU3_PBC, 5.8, 12)  # 16 tiles of 128 sites
+    small = (3, [4, 4, 4, 4], su3.SU3_PBC, 6.0, 60)  # 1 tile, outlives the big job
+    srv = su3.Server(max_slots=4)
+    ib = srv.submit(job_config(*big[:4]), big[4])
+    t0 = time.time()
+    while srv.stats()[0] < 1 and time.time() - t0 < 30:  # the graph is captured in the big job's first round
+        time.sleep(0.001)
+    js = srv.submit(job_config(*small[:4]), small[4])
+    rb, rs = srv.wait(ib, timeout_s=60), srv.wait(js, timeout_s=60)
+    srv.close()
+    assert rb.status == su3.SU3_OK and rs.status == su3.SU3_OK
+    for job, r in ((big, rb), (small, rs)):
+        plaq, poly, (prop, acc, _) = alone(*job)
+        assert abs(r.plaquette[0] - plaq[0]) < 1e-14
+        assert (r.proposals, r.accepts) == (prop, acc)
+
+
 def test_admission_waits_for_memory():
     cfg = job_config(0, [16, 16, 16, 16], su3.SU3_PBC, 6.0)
     one_job = su3.su3_link_bytes(cfg)
