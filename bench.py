@@ -649,7 +649,13 @@ def main():
             nres = 5 * (lat.nlayers + 1)
             outs = [torch.empty(nres, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
             evs = [torch.cuda.Event() for _ in range(2)]
-            lat.sweep(SWEEPS_PER_STEP)  # warm
+            # untimed warm-up steps of the same cycle: the first copies from a
+            # freshly pinned buffer ran at 40-55 GB/s against ~210 GB/s after
+            for _ in range(2):
+                lat.stage_links(host, fmt=fmt)
+                lat.apply_links()
+                lat.sweep(SWEEPS_PER_STEP)
+                lat.latest_measurement_async(outs[0])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             lat.stage_links(host, fmt=fmt)
