@@ -437,6 +437,9 @@ struct Engine {
   bool weighted_any = false;  // some chain has two couplings: the tick kernel's weighted form
   bool sub_any = false;       // the (only) chain is divided into sublattice boxes
   bool torus_all = false;     // every chain is an undivided periodic 4-D torus, one coupling, default key
+  // the tick kernel's torus form: 0 none, 1 the torus form, 2 its form for several chains
+  int torus_form() const { return torus_all ? (chains.size() > 1 ? 2 : 1) : 0; }
+  int torus_form_built = 0;   // the form the captured graph launches
   cudaStream_t stream = nullptr;
   std::vector<Chain> chains;
   // device mirrors
@@ -737,6 +740,10 @@ struct Engine {
       torus_all = tor;
       drop_graph();
     }
+    if (torus_form() != torus_form_built) {  // one chain <-> several: the torus form changes too
+      torus_form_built = torus_form();
+      drop_graph();
+    }
     if (chains.size() > chain_cap) {
       cudaFree(d_desc);
       cudaFree(d_state);
@@ -841,12 +848,12 @@ struct Engine {
 
   // One tick, and for a divided chain the halo refresh of what it changed.
   su3_status one_tick(int grid) {
-    cudaError_t e = launch_tick(storage, variant, weighted_any, sub_any, torus_all, args(), grid, block, stream, pdl);
+    cudaError_t e = launch_tick(storage, variant, weighted_any, sub_any, torus_form(), args(), grid, block, stream, pdl);
     if (e != cudaSuccess && pdl) {  // not offered here: plain launches from now on
       cudaGetLastError();
       pdl = false;
       drop_graph();
-      e = launch_tick(storage, variant, weighted_any, sub_any, torus_all, args(), grid, block, stream, false);
+      e = launch_tick(storage, variant, weighted_any, sub_any, torus_form(), args(), grid, block, stream, false);
     }
     CU(e);
     if (sub_any) CU(halo_refresh(d_desc, d_state, 0));
@@ -905,7 +912,7 @@ struct Engine {
     cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     for (int i = 0; i < kGraphTicks && e == cudaSuccess; ++i) {
-      e = launch_tick(storage, variant, weighted_any, sub_any, torus_all, args(), grid, block, stream, pdl);
+      e = launch_tick(storage, variant, weighted_any, sub_any, torus_form(), args(), grid, block, stream, pdl);
       if (e == cudaSuccess && sub_any) e = halo_refresh(d_desc, d_state, 0);
     }
     cudaError_t e2 = cudaStreamEndCapture(stream, &g);
@@ -1515,7 +1522,7 @@ static su3_status autotune_engine(Engine &e, int *variant, int *threads, int *ct
     for (int t : cand_t) {
       if (t > tick_max_threads(e.storage, v)) continue;
       int occ = 0;
-      if (tick_occupancy(e.storage, v, e.weighted_any, e.sub_any, e.torus_all, t, &occ) != cudaSuccess || occ < 1) continue;
+      if (tick_occupancy(e.storage, v, e.weighted_any, e.sub_any, e.torus_form(), t, &occ) != cudaSuccess || occ < 1) continue;
       // 0 = one CTA per tile, then persistent grids of 1, 2, 4, ..., occ CTAs per SM
       for (int c = 0; c <= occ && st == SU3_OK; c = (c == 0) ? 1 : ((c < occ && 2 * c > occ) ? occ : 2 * c)) {
         if ((st = e.set_launch(v, t, c)) != SU3_OK) break;
@@ -1787,7 +1794,7 @@ extern "C" su3_status su3_server_create(size_t hbm_budget_bytes, int max_slots, 
     // persistent grid: its size does not depend on the resident jobs, so the
     // captured graph of ticks survives admissions and retirements
     int occ = 0;
-    if (tick_occupancy(SU3_FP32_12, srv->eng.variant, false, false, false, srv->eng.block, &occ) != cudaSuccess || occ < 1) occ = 1;
+    if (tick_occupancy(SU3_FP32_12, srv->eng.variant, false, false, 0, srv->eng.block, &occ) != cudaSuccess || occ < 1) occ = 1;
     srv->eng.ctas_per_sm = occ;
   }
   if (cudaEventCreate(&srv->round_ev[0]) != cudaSuccess || cudaEventCreate(&srv->round_ev[1]) != cudaSuccess) {

@@ -704,6 +704,45 @@ __device__ __forceinline__ void load_chain(const EngineArgs &ea, int c, ChainDes
   }
 }
 
+// The next chain of a CTA, staged in shared memory (multi-chain form).
+struct ChainStaging {
+  ChainDesc d;
+  ChainState s;
+};
+struct NoStaging {};
+
+// Start asynchronous copies (cp.async, one 4-byte word per thread at a
+// time) of chain c's descriptor and current state into the CTA's staging
+// buffer.  The CTA's next chain switch waits for them (cp.async.wait_all,
+// then the barrier) and copies them over the current ones, instead of
+// waiting behind that barrier for a round trip to L2.
+__device__ __forceinline__ void stage_chain(const EngineArgs &ea, int c, int par, ChainStaging &stg) {
+  const int n1 = sizeof(ChainDesc) / 4, n2 = sizeof(ChainState) / 4;
+  const uint32_t *src1 = reinterpret_cast<const uint32_t *>(ea.desc + c);
+  const uint32_t *src2 = reinterpret_cast<const uint32_t *>(ea.state + 2 * (size_t)c + par);
+  uint32_t *dst1 = reinterpret_cast<uint32_t *>(&stg.d), *dst2 = reinterpret_cast<uint32_t *>(&stg.s);
+  for (int i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
+    const uint32_t *src = i < n1 ? src1 + i : src2 + (i - n1);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(i < n1 ? dst1 + i : dst2 + (i - n1));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Copy the staged descriptor and state over the current ones (shared to
+// shared, one word per thread at a time).
+__device__ __forceinline__ void take_staged(ChainDesc &sd, ChainState &ss, const ChainStaging &stg) {
+  const int n1 = sizeof(ChainDesc) / 4, n2 = sizeof(ChainState) / 4;
+  const uint32_t *src1 = reinterpret_cast<const uint32_t *>(&stg.d), *src2 = reinterpret_cast<const uint32_t *>(&stg.s);
+  uint32_t *dst1 = reinterpret_cast<uint32_t *>(&sd), *dst2 = reinterpret_cast<uint32_t *>(&ss);
+  for (int i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
+    if (i < n1)
+      dst1[i] = src1[i];
+    else
+      dst2[i - n1] = src2[i - n1];
+  }
+}
+
 // Warp-sum the FHKP counters and add them to the chain's totals.
 __device__ __forceinline__ void flush_counters(const ChainDesc &d, uint32_t &np, uint32_t &na) {
 #pragma unroll
@@ -804,12 +843,21 @@ template <> struct TickBounds<10> { static constexpr int kThreads = 256, kMinBlo
 // beta1 != beta); unweighted chains compute identically in both forms.
 // SUB: compiled for a chain divided into sublattice boxes (one chain per
 // engine); a halo refresh follows every launch.
+// MC (with TOR, FP32 12-real variant 0 only): compiled for such engines with
+// several chains.  A CTA's tiles then belong to a new chain almost every
+// time (tiles are dealt out in grid-stride order), and each switch waited
+// behind a CTA barrier for the new descriptor's round trip to L2; this form
+// stages the chain of the CTA's next tile in shared memory with cp.async
+// while the current tile runs.  It is a form of its own because the
+// staging code, even when not executed, slowed the single-chain update by
+// 0.6 %.
 // TOR: compiled for engines whose chains are all undivided periodic 4-D tori
 // with one coupling and the default random-number key (the benchmark's
 // lattices and most ensembles): the unrolled update with D, the layer and
 // the site key fixed at compile time.
-template <class S, int V, bool WT, bool SUB = false, bool TOR = false>
+template <class S, int V, bool WT, bool SUB = false, bool TOR = false, bool MC = false>
 __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBlocks) k_tick(EngineArgs ea) {
+  __shared__ std::conditional_t<MC, ChainStaging, NoStaging> stg;
   __shared__ ChainDesc sd;
   __shared__ ChainState ss;  // the current chain's current state
   __shared__ int s_par;      // the state slot that holds the current states
@@ -825,14 +873,32 @@ __global__ void __launch_bounds__(TickBounds<V>::kThreads, TickBounds<V>::kMinBl
   int cur = -1;
   uint32_t np = 0, na = 0;  // FHKP counters of the current chain, flushed per warp
   bool wrote_partials = false;  // this thread wrote data that the last warp reads
+  bool staged = false;  // (MC) stg holds the chain of this CTA's next tile
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     const int c = __ldg(ea.tile_chain + t);  // the same for every thread of the CTA
+    int cn = -1;  // (MC) the chain of the CTA's next tile
+    if constexpr (MC) cn = t + (int)gridDim.x < total ? __ldg(ea.tile_chain + t + gridDim.x) : -1;
     if (c != cur) {
       if (cur >= 0) flush_counters(sd, np, na);
-      __syncthreads();  // every warp is done with the previous descriptor
-      load_chain(ea, c, sd, ss, s_par);
+      if constexpr (MC)
+        if (staged) asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncthreads();  // every warp is done with the previous descriptor (MC: staged copies visible)
+      if constexpr (MC) {
+        if (staged)
+          take_staged(sd, ss, stg);
+        else
+          load_chain(ea, c, sd, ss, s_par);
+      } else {
+        load_chain(ea, c, sd, ss, s_par);
+      }
       __syncthreads();
       cur = c;
+    }
+    if constexpr (MC) {
+      // the next tile belongs to another chain: stage it now (its buffer was
+      // last read between the barriers above)
+      staged = cn >= 0 && cn != c;
+      if (staged) stage_chain(ea, cn, s_par, stg);
     }
     if (!ss.active) continue;
     const int lt = t - sd.tile_base;
@@ -1424,10 +1490,10 @@ int tick_variants(int storage) { return storage == 1 ? 5 : 1; }
 // pdl: launch as a programmatic dependent of the previous kernel in the
 // stream (the tick waits for that kernel's completion and memory at its
 // first instruction, so only the launch itself overlaps the previous tick).
-template <class S, int V, bool WT, bool SUB = false, bool TOR = false>
+template <class S, int V, bool WT, bool SUB = false, bool TOR = false, bool MC = false>
 static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_t st, bool pdl) {
   if (!pdl) {
-    k_tick<S, V, WT, SUB, TOR><<<grid, block, 0, st>>>(ea);
+    k_tick<S, V, WT, SUB, TOR, MC><<<grid, block, 0, st>>>(ea);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -1440,12 +1506,12 @@ static cudaError_t tick_v(const EngineArgs &ea, int grid, int block, cudaStream_
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_tick<S, V, WT, SUB, TOR>, ea);
+  return cudaLaunchKernelEx(&cfg, k_tick<S, V, WT, SUB, TOR, MC>, ea);
 }
 
-template <class S, int V, bool WT, bool SUB = false, bool TOR = false>
+template <class S, int V, bool WT, bool SUB = false, bool TOR = false, bool MC = false>
 static cudaError_t occ_v(int block, int *ctas) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<S, V, WT, SUB, TOR>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_tick<S, V, WT, SUB, TOR, MC>, block, 0);
 }
 
 int tick_max_threads(int storage, int variant) {
@@ -1460,40 +1526,44 @@ int tick_max_threads(int storage, int variant) {
   }
 }
 
-// One switch for launching and for occupancy queries: OP<S, V, WT, SUB, TOR>.
+// One switch for launching and for occupancy queries: OP<S, V, WT, SUB, TOR, MC>.
+// torus: 0 none, 1 the torus form, 2 the torus form for several chains.
 // The torus form exists for the unrolled float variants (FP32 12-real 0 and
-// 1, FP32 18-real 0); the others ignore `tor`.
-template <template <class, int, bool, bool, bool> class OP, bool WT, class... A>
-static cudaError_t tick_dispatch(int storage, int variant, bool sub, bool tor, A... a) {
-  tor = tor && !sub && !WT;
-  if (storage == 0) return sub ? OP<StoreF64x18, 10, WT, true, false>::run(a...) : OP<StoreF64x18, 10, WT, false, false>::run(a...);
+// 1, FP32 18-real 0), its multi-chain form for FP32 12-real variant 0 (the
+// others run the plain torus form); the remaining forms ignore `torus`.
+template <template <class, int, bool, bool, bool, bool> class OP, bool WT, class... A>
+static cudaError_t tick_dispatch(int storage, int variant, bool sub, int torus, A... a) {
+  const bool tor = torus != 0 && !sub && !WT, mc = tor && torus == 2;
+  if (storage == 0) return sub ? OP<StoreF64x18, 10, WT, true, false, false>::run(a...) : OP<StoreF64x18, 10, WT, false, false, false>::run(a...);
   if (storage == 2) {
-    if (sub) return OP<StoreF32x18, kSubVariant, WT, true, false>::run(a...);
-    return tor ? OP<StoreF32x18, 0, false, false, true>::run(a...) : OP<StoreF32x18, 0, WT, false, false>::run(a...);
+    if (sub) return OP<StoreF32x18, kSubVariant, WT, true, false, false>::run(a...);
+    return tor ? OP<StoreF32x18, 0, false, false, true, false>::run(a...) : OP<StoreF32x18, 0, WT, false, false, false>::run(a...);
   }
-  if (sub) return OP<StoreF32x12, kSubVariant, WT, true, false>::run(a...);
+  if (sub) return OP<StoreF32x12, kSubVariant, WT, true, false, false>::run(a...);
   switch (variant) {
-    case 0: return tor ? OP<StoreF32x12, 0, false, false, true>::run(a...) : OP<StoreF32x12, 0, WT, false, false>::run(a...);
-    case 1: return tor ? OP<StoreF32x12, 1, false, false, true>::run(a...) : OP<StoreF32x12, 1, WT, false, false>::run(a...);
-    case 2: return OP<StoreF32x12, 2, WT, false, false>::run(a...);
-    case 3: return OP<StoreF32x12, 3, WT, false, false>::run(a...);
-    default: return OP<StoreF32x12, 4, WT, false, false>::run(a...);
+    case 0:
+      if (mc) return OP<StoreF32x12, 0, false, false, true, true>::run(a...);
+      return tor ? OP<StoreF32x12, 0, false, false, true, false>::run(a...) : OP<StoreF32x12, 0, WT, false, false, false>::run(a...);
+    case 1: return tor ? OP<StoreF32x12, 1, false, false, true, false>::run(a...) : OP<StoreF32x12, 1, WT, false, false, false>::run(a...);
+    case 2: return OP<StoreF32x12, 2, WT, false, false, false>::run(a...);
+    case 3: return OP<StoreF32x12, 3, WT, false, false, false>::run(a...);
+    default: return OP<StoreF32x12, 4, WT, false, false, false>::run(a...);
   }
 }
 
-template <class S, int V, bool WT, bool SUB, bool TOR>
+template <class S, int V, bool WT, bool SUB, bool TOR, bool MC = false>
 struct TickLaunch {
   static cudaError_t run(const EngineArgs *ea, int grid, int block, cudaStream_t st, bool pdl) {
-    return tick_v<S, V, WT, SUB, TOR>(*ea, grid, block, st, pdl);
+    return tick_v<S, V, WT, SUB, TOR, MC>(*ea, grid, block, st, pdl);
   }
 };
 
-template <class S, int V, bool WT, bool SUB, bool TOR>
+template <class S, int V, bool WT, bool SUB, bool TOR, bool MC = false>
 struct TickOccupancy {
-  static cudaError_t run(int block, int *ctas) { return occ_v<S, V, WT, SUB, TOR>(block, ctas); }
+  static cudaError_t run(int block, int *ctas) { return occ_v<S, V, WT, SUB, TOR, MC>(block, ctas); }
 };
 
-cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, bool torus, const EngineArgs &ea, int grid,
+cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, int torus, const EngineArgs &ea, int grid,
                         int block, cudaStream_t st, bool pdl) {
   if (sub) variant = storage == 0 ? 0 : kSubVariant;
   if (block > tick_max_threads(storage, variant)) return cudaErrorInvalidConfiguration;
@@ -1560,7 +1630,7 @@ cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, doub
   });
 }
 
-cudaError_t tick_occupancy(int storage, int variant, bool weighted, bool sub, bool torus, int block, int *ctas_per_sm) {
+cudaError_t tick_occupancy(int storage, int variant, bool weighted, bool sub, int torus, int block, int *ctas_per_sm) {
   *ctas_per_sm = 0;
   if (sub) variant = storage == 0 ? 0 : kSubVariant;
   if (block > tick_max_threads(storage, variant)) return cudaSuccess;

@@ -15,10 +15,11 @@ namespace su3g {
 // sublattice boxes (it fixes the variant: 3 for FP32).
 int tick_variants(int storage);
 int tick_max_threads(int storage, int variant);
-// torus: every chain is an undivided periodic 4-D torus with one coupling
-// and the default random-number key (a form with these fixed at compile
-// time; ignored where no such form exists).
-cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, bool torus, const EngineArgs &ea, int grid,
+// torus: 1 (2 with several chains) when every chain is an undivided
+// periodic 4-D torus with one coupling and the default random-number key
+// (a form with these fixed at compile time; 2 also stages a CTA's next
+// chain in shared memory), 0 otherwise; ignored where no such form exists.
+cudaError_t launch_tick(int storage, int variant, bool weighted, bool sub, int torus, const EngineArgs &ea, int grid,
                         int block, cudaStream_t st, bool pdl = false);
 // Halo refresh of a divided chain (after its tick, or all links), and the
 // copies between its sublattice boxes and the undivided layout.
@@ -33,7 +34,7 @@ cudaError_t launch_convert(int storage, ChainDesc *desc_dev, size_t nlinks, doub
                            cudaStream_t st);
 // Links from rows 1, 2 in float (12 per link, canonical order; 16-byte aligned).
 cudaError_t launch_convert_rows2(int storage, ChainDesc *desc_dev, size_t nlinks, const float *src, cudaStream_t st);
-cudaError_t tick_occupancy(int storage, int variant, bool weighted, bool sub, bool torus, int block, int *ctas_per_sm);
+cudaError_t tick_occupancy(int storage, int variant, bool weighted, bool sub, int torus, int block, int *ctas_per_sm);
 void host_advance_stage(const ChainDesc &d, ChainState &s);
 // Fixed-order sum of n booked action-change slots into *out (device).
 cudaError_t launch_action_sum(const double *slots, int n, double *out, cudaStream_t st);
