@@ -137,6 +137,31 @@ def test_ensemble_matches_sequential_single_chains_256x8x8x8x8():
         assert np.array_equal(ens.get_links(i), alone.get_links())
 
 
+def test_staged_chain_switches_in_a_persistent_torus_ensemble():
+    """A persistent grid (one CTA per SM) over 64 torus chains of 16 tiles:
+    nearly every tile of a CTA belongs to another chain, so the multi-chain
+    torus form stages the next chain's descriptor and state in shared memory
+    at every tile.  Links equal each chain alone bit for bit, and the
+    measurements (every 2 sweeps, finished by the launch's last warp from
+    the list of measuring chains) agree."""
+    rng = np.random.default_rng(7)
+    betas = rng.uniform(5.6, 6.4, 64)
+    kw = dict(storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT, hits=2, reunit_every=3, measure_every=2)
+    cfgs = [su3.make_config([8, 8, 8, 8], beta=float(b), seed=7000 + i, **kw) for i, b in enumerate(betas)]
+    ens = su3.Ensemble(cfgs)
+    ens.set_launch(128, 1, variant=0)
+    ens.sweep(5)
+    for i in [0, 1, 31, 63]:
+        alone = su3.Lattice([8, 8, 8, 8], beta=float(betas[i]), seed=7000 + i, **kw)
+        alone.sweep(5)
+        assert np.array_equal(ens.get_links(i), alone.get_links()), i
+        m_ens, m_alone = ens.measurements(i), alone.measurements()
+        assert m_ens.shape == m_alone.shape == (2, 2, 5)
+        np.testing.assert_allclose(m_ens, m_alone, rtol=0, atol=1e-14)
+        alone.close()
+    ens.close()
+
+
 def test_measurement_stage_records_every_k_sweeps():
     lat = su3.Lattice([6, 6, 6, 6], beta=6.0, seed=2, storage=su3.SU3_FP32_12, start=su3.SU3_START_HOT,
                       reunit_every=2, measure_every=3, measure_capacity=8)
